@@ -1,0 +1,201 @@
+"""Physics pins of the CPU oracle's full step (Sec. 2.2 procedure) against what
+the model fixes: the initial state reproduces its moments (Eq. conservedVariable
+with Eq. auxf a), mass conservation (Eq. locallyconserved), the rest state as a
+fixed point, lattice symmetries, the viscosity definition nu = c_s^2 tau_f
+(Eq. kineticandmobility) by shear-wave decay, the mobility by the linear
+Cahn-Hilliard decay rate, Laplace's law (Sec. 3.1) and the layered Poiseuille
+profile (Sec. 3.2)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1802_02868_gb300 import inputs as I
+
+
+def _smooth(rng, mesh, scale):
+    xc, yc = mesh.centres()
+    X, Y = np.meshgrid(xc, yc)
+    Lx, Ly = mesh.dx.sum(), mesh.dy.sum()
+    out = np.zeros_like(X)
+    for _ in range(3):
+        kx, ky = rng.integers(1, 3, size=2)
+        out += rng.normal() * np.cos(2 * math.pi * kx * X / Lx + rng.uniform(0, 6)) * np.cos(
+            2 * math.pi * ky * Y / Ly + rng.uniform(0, 6))
+    return scale * out
+
+
+def test_init_reproduces_moments():
+    """Step 1 sets tilde = eq - dt/2 F, so Eqs. (phi), (u), (P) give back phi, u, p."""
+    rng = np.random.default_rng(11)
+    mesh = I.Mesh(1.0 + 0.3 * rng.random(10), I.tanh_channel_heights(12, 12.0), I.PERIODIC, I.WALL)
+    beta, kappa = I.params_from_sigma_width(1e-3, 4.0)
+    prm = I.Params(rhoA=2.0, rhoB=0.5, nuA=0.1, nuB=0.3, beta=beta, kappa=kappa, gy=-1e-5, rho_ref=0.5)
+    phi = 0.5 + 0.4 * np.tanh(_smooth(rng, mesh, 1.0))
+    ux, uy, p = (_smooth(rng, mesh, 1e-3) for _ in range(3))
+    o = oracle.Oracle(mesh, prm).init(phi, ux, uy, p)
+    m = o.moments()
+    np.testing.assert_allclose(m["phi"], phi, atol=1e-15)
+    np.testing.assert_allclose(m["ux"], ux, atol=1e-16)
+    np.testing.assert_allclose(m["uy"], uy, atol=1e-16)
+    np.testing.assert_allclose(m["p"], p, atol=1e-16)
+    np.testing.assert_allclose(m["rho"], 0.5 + 1.5 * phi, atol=1e-15)
+
+
+@pytest.mark.parametrize("bcx,bcy", [(I.PERIODIC, I.PERIODIC), (I.PERIODIC, I.WALL), (I.WALL, I.WALL)])
+def test_rest_state_is_fixed_point(bcx, bcy):
+    mesh = I.Mesh(np.array([1.0, 0.7, 1.3, 1.0, 0.9]), np.array([0.8, 1.0, 1.2, 1.0]), bcx, bcy)
+    prm = I.Params(rhoA=3.0, rhoB=1.0, beta=0.003, kappa=0.006)
+    for phi0 in (1.0, 0.0):
+        o = oracle.Oracle(mesh, prm).init(np.full((4, 5), phi0))
+        f0, g0 = o.state()
+        o.step(20)
+        f1, g1 = o.state()
+        np.testing.assert_allclose(f1, f0, atol=1e-16)
+        np.testing.assert_allclose(g1, g0, atol=1e-15)
+
+
+@pytest.mark.parametrize("case", ["drop_periodic", "rt_walls", "nonuniform_walls"])
+def test_order_parameter_conserved(case):
+    """Sum |V| phi is conserved to round-off: interior fluxes telescope, wall
+    zeroth-moment fluxes vanish, and sum_i g~+_i = phi."""
+    if case == "drop_periodic":
+        c = I.stationary_drop(n=32, radius=8.0)
+    elif case == "rt_walls":
+        c = I.rayleigh_taylor(nx=16, ny=48, amplitudes=[2.0])
+    else:
+        c = I.layered_poiseuille(nx=6, ny=24, height=24.0, nu_ratio=10.0, nuB=0.1, force=1e-5)
+        c.phi0 = c.phi0 + 0.05 * np.sin(np.arange(6) / 6 * 2 * math.pi)[None, :]
+    o = oracle.Oracle(c.mesh, c.params).init(c.phi0)
+    s0 = o.conservation()[0]
+    o.step(400)
+    s1 = o.conservation()[0]
+    assert abs(s1 - s0) <= 2e-13 * abs(s0)
+
+
+def test_drop_keeps_square_symmetry():
+    """A centred drop on a uniform periodic mesh keeps the D4 symmetry of the lattice."""
+    c = I.stationary_drop(n=24, radius=7.0, density_ratio=3.0)
+    o = oracle.Oracle(c.mesh, c.params).init(c.phi0)
+    o.step(200)
+    m = o.moments()
+    phi, ux, uy = m["phi"], m["ux"], m["uy"]
+    # the drop centre sits on a cell corner (12,12); reflections map cell i -> 23 - i
+    np.testing.assert_allclose(phi, phi[:, ::-1], atol=1e-13)
+    np.testing.assert_allclose(phi, phi[::-1, :], atol=1e-13)
+    np.testing.assert_allclose(phi, phi.T, atol=1e-13)
+    np.testing.assert_allclose(ux, -ux[:, ::-1], atol=1e-16)
+    np.testing.assert_allclose(ux, uy.T, atol=1e-16)
+    assert np.abs(ux).max() > 1e-9
+
+
+def test_translation_equivariance_on_periodic_mesh():
+    rng = np.random.default_rng(12)
+    mesh = I.uniform_mesh(16, 12)
+    beta, kappa = I.params_from_sigma_width(1e-3, 4.0)
+    prm = I.Params(rhoA=2.0, rhoB=1.0, beta=beta, kappa=kappa, gx=1e-5, gy=-2e-5, rho_ref=1.0)
+    phi = 0.5 + 0.45 * np.tanh(_smooth(rng, mesh, 2.0))
+    a = oracle.Oracle(mesh, prm).init(phi)
+    b = oracle.Oracle(mesh, prm).init(np.roll(phi, (3, 5), (0, 1)))
+    a.step(30)
+    b.step(30)
+    fa, ga = a.state()
+    fb, gb = b.state()
+    np.testing.assert_allclose(np.roll(fa, (3, 5), (1, 2)), fb, atol=1e-15)
+    np.testing.assert_allclose(np.roll(ga, (3, 5), (1, 2)), gb, atol=1e-14)
+
+
+def test_shear_wave_decays_at_nu_k2():
+    """Single phase: u_x = U sin(k y) decays at rate nu k^2 with nu = c_s^2 tau_f
+    (Eq. kineticandmobility; no -1/2 as in lattice Boltzmann)."""
+    ny, nu = 32, 0.05
+    mesh = I.uniform_mesh(1, ny)
+    prm = I.Params(rhoA=1, rhoB=1, nuA=nu, nuB=nu, beta=0.003, kappa=0.006)
+    _, yc = mesh.centres()
+    k = 2 * math.pi / ny
+    o = oracle.Oracle(mesh, prm).init(np.ones((ny, 1)), ux=1e-3 * np.sin(k * yc)[:, None])
+    amps, ts = [], []
+    for s in range(6):
+        o.step(100)
+        amps.append(2 / ny * np.sum(o.moments()["ux"][:, 0] * np.sin(k * yc)))
+        ts.append((s + 1) * 100 * o.dt)
+    rate = -math.log(amps[-1] / amps[1]) / (ts[-1] - ts[1])
+    assert rate == pytest.approx(nu * k * k, rel=0.015)
+
+
+def test_cahn_hilliard_linear_decay_rate():
+    """phi = phiA + eps cos(kx), equal densities.  Linearising Eq. (CH0), the pressure
+    relation of Appendix A (Eq. continuity-equation) and the momentum balance
+    grad p = -phi grad mu gives the rate lambda k^2 a / (1 + a / c_s^2) with
+    a = psi''(phiA) + kappa k^2 = 2 beta (phiA - phiB)^2 + kappa k^2."""
+    nx, lam = 32, 1.0
+    mesh = I.uniform_mesh(nx, 1)
+    beta, kappa = I.params_from_sigma_width(1e-3, 4.0)
+    prm = I.Params(rhoA=1, rhoB=1, nuA=1.0, nuB=1.0, mobility=lam, tau_g=0.5, beta=beta, kappa=kappa)
+    xc, _ = mesh.centres()
+    k, eps = 2 * math.pi / nx, 1e-3
+    a = 2 * beta + kappa * k * k
+    o = oracle.Oracle(mesh, prm).init((1 + eps * np.cos(k * xc))[None, :], p=-(a * eps * np.cos(k * xc))[None, :])
+    n = int(400 / o.dt)
+    amps, ts = [], []
+    for s in range(5):
+        o.step(n)
+        amps.append(2 / nx * np.sum((o.moments()["phi"][0] - 1) * np.cos(k * xc)))
+        ts.append((s + 1) * n * o.dt)
+    rate = -math.log(amps[-1] / amps[0]) / (ts[-1] - ts[0])
+    assert rate == pytest.approx(lam * k * k * a / (1 + 3 * a), rel=0.03)
+
+
+def test_flat_interface_chemical_potential_small():
+    """The tanh profile (Eq. equilibriuminterface) solves mu = 0 in the continuum; the
+    discrete mu stays a small fraction of the bulk term's scale."""
+    c = I.layered_poiseuille(nx=2, ny=48, height=48.0, nuB=0.1, force=0.0)
+    o = oracle.Oracle(c.mesh, c.params).init(c.phi0)
+    o.moments()
+    mu = o.aux()["mu"]
+    scale = c.params.beta * 0.25  # max |psi'| over [0,1] is beta/(3 sqrt 3) ~ 0.19 beta
+    assert np.abs(mu).max() < 0.05 * scale
+
+
+@pytest.mark.slow
+def test_laplace_law():
+    """Delta p = sigma / R for stationary drops (Sec. 3.1), bulk pressures (where the
+    Laplace pressure P reduces to p), equal densities, two radii."""
+    dps = {}
+    for R in (12.0, 16.0):
+        c = I.stationary_drop(n=48, radius=R, nu=0.5, density_ratio=1.0, sigma=1e-3)
+        o = oracle.Oracle(c.mesh, c.params).init(c.phi0)
+        o.step(2000)
+        p = o.moments()["p"]
+        dps[R] = p[24, 24] - p[0, 0]
+        assert dps[R] * R / 1e-3 == pytest.approx(1.0, abs=0.06)
+    assert dps[12.0] / dps[16.0] == pytest.approx(16.0 / 12.0, rel=0.03)
+
+
+def _two_layer_profile(y, H, G, muA, muB):
+    """Analytic layered-Poiseuille profile of Sec. 3.2 with walls at y = 0, H and fluid A
+    below y = H/2 (the paper's coordinate is reversed: Y = H/2 - y)."""
+    Hp = H / 2
+    Y = Hp - y
+    r = (muA - muB) / (muA + muB)
+    uA = G * Hp ** 2 / (2 * muA) * (-(Y / Hp) ** 2 - (Y / Hp) * r + 2 * muA / (muA + muB))
+    uB = G * Hp ** 2 / (2 * muB) * (-(Y / Hp) ** 2 - (Y / Hp) * r + 2 * muB / (muA + muB))
+    return np.where(Y >= 0, uA, uB)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("ratio,tol", [(1.0, 0.005), (10.0, 0.05)])
+def test_layered_poiseuille_profile(ratio, tol):
+    """Steady two-layer channel flow on the tanh-refined mesh matches the analytic
+    profile; started from it, the scheme stays within the diffuse-interface error."""
+    H, G = 48.0, 1e-7
+    c = I.layered_poiseuille(nx=2, ny=48, height=H, nu_ratio=ratio, nuB=0.05, force=G)
+    _, yc = c.mesh.centres()
+    ua = _two_layer_profile(yc, H, G, c.params.nuA, c.params.nuB)
+    o = oracle.Oracle(c.mesh, c.params).init(c.phi0, ux=np.repeat(ua[:, None], 2, axis=1))
+    o.step(12000)
+    un = o.moments()["ux"][:, 0]
+    assert np.linalg.norm(un - ua) / np.linalg.norm(ua) < tol
+    # and from rest, the centre-line velocity approaches u_c = G Hp^2 / (muA + muB)
+    assert ua[23] == pytest.approx(G * (H / 2) ** 2 / (c.params.nuA + c.params.nuB), rel=0.02)
