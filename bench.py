@@ -1,0 +1,310 @@
+"""Benchmark of the two-phase DUGKS step on GB300.
+
+Default workload: the batched ensemble of 512 rising-bubble / stationary-drop
+instances on square periodic meshes of uneven side (64..512, seed 1802), FP32
+storage, ~3.96e7 cells.  One "step" advances every instance of the batch by
+one time step (all rows of the hot path).  The metric is cell-updates/s (one
+cell advancing both D2Q9 distributions f and g by one dt).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload batch|rt|drop|roofline] [--precision fp32|fp64]
+
+For N > 1 (launched with torch.distributed.run) every rank advances its own
+ensemble (seed 1802 + rank): weak scaling with no data-path collective.
+The reference arm (--impl reference) times the CPU FP64 oracle on a bounded
+sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1802_02868_gb300 import inputs as I  # noqa: E402
+
+METRIC = "cell-updates/s (f+g, D2Q9)"
+UNIT = "cell-updates/s"
+
+
+def workload(name, seed):
+    if name == "batch":
+        cases = I.batched_ensemble(512, seed=seed)
+        desc = {"workload": "batched ensemble: 512 rising-bubble/stationary-drop instances, square periodic "
+                            "meshes side in {64..512}, density ratio log-uniform [2, 20], seed %d" % seed,
+                "instances": 512}
+    elif name == "rt":
+        cases = [I.rayleigh_taylor()]
+        desc = {"workload": "Rayleigh-Taylor 256x1024, At=0.5, Re=3000, walls in y", "instances": 1}
+    elif name == "drop":
+        cases = [I.stationary_drop()]
+        desc = {"workload": "stationary drop 64x64 periodic, rho ratio 10", "instances": 1}
+    elif name == "roofline":
+        cases = [I.roofline_drop()]
+        desc = {"workload": "roofline drop 4096x4096 periodic, R=1024", "instances": 1}
+    else:
+        raise SystemExit("unknown workload %s" % name)
+    desc["cells"] = int(sum(c.mesh.ncells for c in cases))
+    return cases, desc
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampler of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if self.p is None:
+            return out
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if sm:
+            out["sm_mhz"] = statistics.median(sm)
+            out["sm_max_mhz"] = max(smax)
+            out["samples"] = len(sm)
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+def measured_peak_hbm():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(cases, precision_name, budget_s=12.0):
+    """Time the CPU FP64 oracle, as it stands, on a bounded sample of the workload."""
+    import oracle
+    sample = cases[: min(len(cases), 4)]
+    sims = [oracle.Oracle(c.mesh, c.params).init(c.phi0) for c in sample]
+    cells = sum(c.mesh.ncells for c in sample)
+    for s in sims:            # one warm step (allocates, faults pages)
+        s.step(1)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        for s in sims:
+            s.step(1, check=False)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": steps * cells / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d of %d instances (%d cells), %d FP64 oracle steps, %.1f s" % (
+                len(sample), len(cases), cells, steps, dt)}
+
+
+def run_reference(args, cases, desc):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    sample = cases[: min(len(cases), 2)]
+    sims = [oracle.Oracle(c.mesh, c.params).init(c.phi0) for c in sample]
+    cells = sum(c.mesh.ncells for c in sample)
+    for _ in range(args.warmup):
+        for s in sims:
+            s.step(1, check=False)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for s in sims:
+            s.step(1, check=False)
+    dt = time.perf_counter() - t0
+    value = args.steps * cells / dt
+    threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(desc, sample_instances=len(sample), sample_cells=cells),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "%d of %d instances per step (%d cells)" % (len(sample), len(cases), cells)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batch", choices=["batch", "rt", "drop", "roofline"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    ws, rank, local = dist_env()
+    cases, desc = workload(args.workload, 1802 + rank)
+    if args.impl == "reference":
+        return run_reference(args, cases, desc)
+
+    import torch
+    from paper_1802_02868_gb300 import dugks
+
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    prec = dugks.FP32 if args.precision == "fp32" else dugks.FP64
+    stream = torch.cuda.current_stream()
+    sim = dugks.Sim([c.mesh for c in cases], [c.params for c in cases], prec, stream=stream.cuda_stream)
+    ncells = sim.ncells
+    # pinned host buffers for the end-to-end leg
+    phi_h = torch.from_numpy(np.concatenate([c.phi0.reshape(-1) for c in cases])).pin_memory()
+    sim.init(phi_h.numpy())
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---- device-resident timed region
+    clocks = Clocks(local)
+    clocks.start()
+    sim.set_timing(True)
+    sim.kernel_times()            # reset the accumulators
+    l0 = sim.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    launches = sim.launch_count() - l0
+    ktimes = sim.kernel_times()
+    sim.set_timing(False)
+    clk = clocks.stop()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    st = sim.status()
+    n_finite = sum(1 for v in st if v == 0)
+    # masked (non-finite) instances do no work: count only the cells advanced
+    live_cells = int(sum(c.mesh.ncells for c, v in zip(cases, st) if v == 0))
+    value = ws * args.steps * live_cells / (ms * 1e-3)
+
+    # ---- end to end through the public API: host phi -> init -> steps with a
+    # per-step FP64 conservation read-back -> moments to host
+    out_h = [torch.empty(ncells, dtype=torch.float64).pin_memory() for _ in range(5)]
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sim.init(phi_h.numpy())
+    for _ in range(args.steps):
+        sim.step(1)
+        sim.conservation()
+    m = sim.moments()
+    for k, name in enumerate(("phi", "rho", "ux", "uy", "p")):
+        arr = np.concatenate([a.reshape(-1) for a in m[name]]) if isinstance(m[name], list) else m[name].reshape(-1)
+        out_h[k].numpy()[:] = arr
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    n_inst = len(cases)
+    h2d = ncells * 8 / args.steps
+    d2h = (2 * 8 * n_inst * args.steps + 5 * 8 * ncells) / args.steps
+    e2e = {"value": ws * args.steps * ncells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h,
+           "note": "init from pinned host phi + K steps each followed by a conservation read-back + moments to host"}
+
+    # ---- roofline of the dominant kernel
+    best = max(range(dugks.NUM_KERNELS), key=lambda k: ktimes[dugks.kernel_name(k)][0])
+    kname = dugks.kernel_name(best)
+    kms, kn = ktimes[kname]
+    avg_s = kms / max(kn, 1) * 1e-3
+    bpc = sim.kernel_bytes_per_cell(best)
+    achieved = bpc * ncells / avg_s / 1e9
+    peak, peak_kind = measured_peak_hbm()
+    roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
+            "bytes_per_cell": bpc, "avg_launch_ms": avg_s * 1e3,
+            "kernel_share": {k: v[0] / max(sum(x[0] for x in ktimes.values()), 1e-12) for k, v in ktimes.items()
+                             if v[1]}}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32" if prec == dugks.FP32 else "f64", "data": "synthetic",
+            "config": dict(desc, precision=args.precision, l2="inputs larger than L2 (state %.2f GB)" % (
+                ncells * 72 * (1 if prec == dugks.FP32 else 2) / 1e9) if ncells * 72 > 129e6 else
+                "inputs smaller than L2: not flushed"),
+            "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk, "instances_finite": n_finite}
+    if rank == 0 and not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_baseline(cases, args.precision)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    sim.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

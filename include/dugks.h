@@ -1,0 +1,148 @@
+/*
+ * dugks.h -- C ABI of the GB300 (sm_103a) two-phase DUGKS library.
+ *
+ * The library advances the discrete unified gas-kinetic scheme for immiscible
+ * two-phase flows of Zhang, Yang & Guo (arXiv:1802.02868): two D2Q9 kinetic
+ * equations, f for pressure and momentum and g for the Cahn-Hilliard order
+ * parameter phi (Sec. 2.2, Eqs. bgkf, bgkg), on tensor-product finite-volume
+ * meshes with per-column and per-row spacings.
+ *
+ * Conventions for every call:
+ *  - All calls return an int status (dugks_status); nothing aborts or exits.
+ *  - Host arrays are caller-owned, read or written during the call, and never
+ *    retained.  Cell fields are row-major [ny][nx] doubles (x fastest); for a
+ *    batch, instance k's cells follow those of instance k-1.
+ *  - Device memory is owned by the library (cudaMalloc at create time, freed
+ *    by dugks_destroy).  The stream is the caller's; all device work of a
+ *    simulation is enqueued on it.
+ *  - Argument errors return DUGKS_ERR_ARG before any device work.  CUDA errors
+ *    return DUGKS_ERR_CUDA.  A single simulation whose state became non-finite
+ *    is reported as DUGKS_ERR_NONFINITE by the next synchronising call.  In a
+ *    batch, an instance that becomes non-finite is masked (its tiles are
+ *    skipped from the next step on) and reported by dugks_batch_status only;
+ *    the other instances continue.
+ */
+#ifndef DUGKS_H
+#define DUGKS_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DUGKS_OK = 0,
+    DUGKS_ERR_ARG = -1,
+    DUGKS_ERR_CUDA = -2,
+    DUGKS_ERR_NONFINITE = -3,
+    DUGKS_ERR_OOM = -4,
+    DUGKS_ERR_TIMEOUT = -5,
+    DUGKS_ERR_UNSUPPORTED = -6
+} dugks_status;
+
+/* Boundary condition per axis: periodic, or bounce-back no-slip walls at both
+   ends of the axis (Sec. 3.2 "no-slip", Sec. 3.4 "bounce-back"). */
+typedef enum { DUGKS_BC_PERIODIC = 0, DUGKS_BC_WALL = 1 } dugks_bc;
+
+/* Storage and arithmetic precision of the distributions. */
+typedef enum { DUGKS_FP64 = 0, DUGKS_FP32 = 1 } dugks_precision;
+
+/* Tensor-product mesh: dx[nx] column widths, dy[ny] row heights, all > 0
+   (Sec. 2.2, cell volume |V| = dx*dy; Sec. 3.2 non-uniform mesh).  Copied at
+   create time.  Wall axes need at least 2 cells. */
+typedef struct {
+    int nx, ny;
+    const double *dx, *dy;
+    int bc_x, bc_y; /* dugks_bc */
+} dugks_mesh;
+
+/* Model parameters (Sec. 2.1-2.2):
+ *  phiA, phiB  order parameter of bulk fluids A and B (phiA != phiB);
+ *  rhoA, rhoB  densities (Eq. oderrho), > 0;
+ *  nuA, nuB    kinematic viscosities, mixed by Eq. mixvis, > 0;
+ *  mobility    lambda of Eq. CH0, >= 0;  tau_g relaxation time of g (> 0),
+ *              eta = lambda / (c_s^2 tau_g) (Eq. kineticandmobility);
+ *  beta, kappa free-energy coefficients (Eqs. doublewell, chemicalpotential);
+ *  gx, gy      body-force acceleration; F_b = (rho - rho_ref) (gx, gy);
+ *  cfl         alpha of Eq. cfl, in (0, 1]; dt = cfl * min(dx, dy) / sqrt(2);
+ *  precision   dugks_precision. */
+typedef struct {
+    double phiA, phiB, rhoA, rhoB, nuA, nuB, mobility, tau_g, beta, kappa, gx, gy, rho_ref, cfl;
+    int precision;
+} dugks_params;
+
+typedef struct dugks_sim dugks_sim; /* opaque, library-owned */
+
+/* Create one simulation on the current CUDA device; stream may be NULL (the
+   legacy default stream).  Validates the mesh and parameters (ERR_ARG),
+   allocates device state (ERR_OOM on failure) and uploads the geometry. */
+int dugks_create(const dugks_mesh *mesh, const dugks_params *params, void *cuda_stream, dugks_sim **out);
+
+/* Create a batch of n independent instances (uneven sizes allowed) advanced
+   together, one launch per kernel per step.  All instances share the
+   precision of params[0]. */
+int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *params, void *cuda_stream,
+                       dugks_sim **out);
+
+void dugks_destroy(dugks_sim *sim);
+
+/* Step 1 of the procedure (Sec. 2.2): set phi, u, p at the cell centres and
+   the tracked distributions tilde = eq - dt/2 F (Eq. auxf a with the original
+   distribution at equilibrium).  Host arrays of all cells; ux, uy, p may be
+   NULL (zero).  Copies host -> device on the sim's stream and synchronises. */
+int dugks_init(dugks_sim *sim, const double *phi, const double *ux, const double *uy, const double *p);
+
+/* Steps 2-7 repeated nsteps times (Sec. 2.2; Eqs. relations1/2, fbar_h,
+   original-function, microfluxf, updatef).  Asynchronous on the sim's stream;
+   a non-finite state is reported by the next synchronising call. */
+int dugks_step(dugks_sim *sim, long nsteps);
+
+/* Macroscopic fields at the cell centres from the current state (Eqs. phi,
+   oderrho, u, P).  Host outputs of all cells, each may be NULL.  Synchronises. */
+int dugks_moments(dugks_sim *sim, double *phi, double *rho, double *ux, double *uy, double *p);
+
+/* FP64 volume-weighted sums of phi and rho per instance (Eq. locallyconserved);
+   arrays of n_instances doubles.  Synchronises. */
+int dugks_conservation(dugks_sim *sim, double *sum_phi, double *sum_rho);
+
+/* Per-instance status (DUGKS_OK or DUGKS_ERR_NONFINITE) since creation or the
+   last init; array of n_instances ints.  Synchronises. */
+int dugks_batch_status(dugks_sim *sim, int *per_instance_status);
+
+/* Time step dt of instance k (Eq. cfl). */
+int dugks_dt(const dugks_sim *sim, int instance, double *dt);
+
+/* Sizes: number of instances, total cells, and the state size in bytes. */
+int dugks_info(const dugks_sim *sim, int *n_instances, long *n_cells, size_t *state_bytes);
+
+/* Checkpoint: copy the tracked state (tilde f and g, all instances, FP64) to a
+   host buffer of *bytes bytes ([2][9][cells] doubles, f first) or restore it.
+   With buf == NULL, dugks_save only reports the size.  Synchronises. */
+int dugks_save(dugks_sim *sim, void *buf, size_t *bytes);
+int dugks_load(dugks_sim *sim, const void *buf, size_t bytes);
+
+/* Counts kernel launches issued by this sim (for the caller's accounting). */
+int dugks_launch_count(const dugks_sim *sim, long *count);
+
+/* Per-kernel timing with CUDA events on the sim's stream: enable (1) or
+   disable (0).  While enabled every launch is bracketed by events; read the
+   accumulated milliseconds and launch counts per kernel with
+   dugks_kernel_times (arrays of DUGKS_NUM_KERNELS entries, names by
+   dugks_kernel_name).  Synchronises on read. */
+#define DUGKS_NUM_KERNELS 6
+int dugks_set_timing(dugks_sim *sim, int enable);
+int dugks_kernel_times(dugks_sim *sim, double *ms, long *launches);
+const char *dugks_kernel_name(int k);
+
+/* Algorithmic bytes one launch of kernel k moves per cell (for roofline
+   accounting), for this sim's precision. */
+int dugks_kernel_bytes_per_cell(const dugks_sim *sim, int k, double *bytes);
+
+const char *dugks_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DUGKS_H */

@@ -1,0 +1,632 @@
+// dugks_api.cu -- host side of the C ABI declared in include/dugks.h:
+// validation, derived parameters, mesh geometry tables, the tile table of a
+// batch, device memory, and the launch sequence of one step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/dugks.h"
+#include "dugks_common.cuh"
+#include "dugks_kernels.cuh"
+
+using namespace dugks;
+
+namespace {
+
+struct EventPair {
+    cudaEvent_t a, b;
+    int kernel;
+};
+
+}  // namespace
+
+struct dugks_sim {
+    int n_inst = 0;
+    int prec = DUGKS_FP64;
+    cudaStream_t stream = nullptr;
+    long long N = 0;          // padded cells of all instances
+    long long n_dense = 0;    // real cells of all instances
+    int n_tiles = 0;
+    std::vector<InstDev> h_inst;
+    std::vector<long long> h_dense0;
+    // device
+    InstDev *d_inst = nullptr;
+    int4 *d_tiles = nullptr;
+    AxisRec *d_geo = nullptr;
+    long long *d_dense0 = nullptr;
+    void *d_planes = nullptr;     // one allocation for all planes of type T
+    double *d_phi = nullptr;      // FP64 order parameter plane
+    int *d_status = nullptr;
+    double2 *d_partials = nullptr;
+    double2 *d_sums = nullptr;
+    double *d_stage = nullptr;    // dense FP64 staging [5][n_dense]
+    Planes<double> P64{};
+    Planes<float> P32{};
+    long launches = 0;
+    bool timing = false;
+    std::vector<EventPair> ev_used;
+    std::vector<cudaEvent_t> ev_pool;
+    double k_ms[K_COUNT] = {0};
+    long k_n[K_COUNT] = {0};
+};
+
+namespace {
+
+const char *kNames[K_COUNT] = {"k_mu", "k_macro", "k_cell", "k_face", "k_init", "k_reduce"};
+
+int cuda_status(cudaError_t e)
+{
+    if (e == cudaSuccess) return DUGKS_OK;
+    if (e == cudaErrorMemoryAllocation) return DUGKS_ERR_OOM;
+    return DUGKS_ERR_CUDA;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+int validate(const dugks_mesh &m, const dugks_params &p)
+{
+    if (m.nx < 1 || m.ny < 1 || !m.dx || !m.dy) return DUGKS_ERR_ARG;
+    if ((m.bc_x != DUGKS_BC_PERIODIC && m.bc_x != DUGKS_BC_WALL) || (m.bc_y != DUGKS_BC_PERIODIC && m.bc_y != DUGKS_BC_WALL))
+        return DUGKS_ERR_ARG;
+    if ((m.bc_x == DUGKS_BC_WALL && m.nx < 2) || (m.bc_y == DUGKS_BC_WALL && m.ny < 2)) return DUGKS_ERR_ARG;
+    if ((long long)m.nx * m.ny > (1LL << 40)) return DUGKS_ERR_ARG;
+    for (int i = 0; i < m.nx; i++) if (!finite_pos(m.dx[i])) return DUGKS_ERR_ARG;
+    for (int j = 0; j < m.ny; j++) if (!finite_pos(m.dy[j])) return DUGKS_ERR_ARG;
+    const double vals[] = {p.phiA, p.phiB, p.rhoA, p.rhoB, p.nuA, p.nuB, p.mobility, p.tau_g,
+                           p.beta, p.kappa, p.gx, p.gy, p.rho_ref, p.cfl};
+    for (double v : vals) if (!std::isfinite(v)) return DUGKS_ERR_ARG;
+    if (p.phiA == p.phiB) return DUGKS_ERR_ARG;
+    if (!finite_pos(p.rhoA) || !finite_pos(p.rhoB) || !finite_pos(p.nuA) || !finite_pos(p.nuB)) return DUGKS_ERR_ARG;
+    if (!finite_pos(p.tau_g) || p.mobility < 0.0) return DUGKS_ERR_ARG;
+    if (!(p.cfl > 0.0 && p.cfl <= 1.0)) return DUGKS_ERR_ARG;
+    const double rr = p.rhoA / p.rhoB;
+    const double den = p.phiA - p.phiB * rr;   // Eq. (Gama) denominator
+    if (den == 0.0 || !std::isfinite((rr - 1.0) / den)) return DUGKS_ERR_ARG;
+    if (p.precision != DUGKS_FP64 && p.precision != DUGKS_FP32) return DUGKS_ERR_ARG;
+    return DUGKS_OK;
+}
+
+// Geometry records of one axis (Eqs. nonphi, nonphi2; mirror ghosts at walls).
+void axis_records(int n, const double *d, int bc, std::vector<AxisRec> &out)
+{
+    const bool wall = bc == DUGKS_BC_WALL;
+    for (int k = 0; k < n; k++) {
+        AxisRec r;
+        std::memset(&r, 0, sizeof(r));
+        r.d = d[k];
+        bool has_m = true, has_p = true;
+        int km, kp;
+        double dl, dr;
+        if (k > 0) { km = k - 1; dl = 0.5 * (d[k] + d[km]); }
+        else if (!wall) { km = n - 1; dl = 0.5 * (d[k] + d[km]); }
+        else { km = k; dl = d[k]; has_m = false; }
+        if (k < n - 1) { kp = k + 1; dr = 0.5 * (d[k] + d[kp]); }
+        else if (!wall) { kp = 0; dr = 0.5 * (d[k] + d[kp]); }
+        else { kp = k; dr = d[k]; has_p = false; }
+        r.km = km;
+        r.kp = kp;
+        // Eq. (nonphi) in distances: (dl^2 F+ + (dl+dr)(dr-dl) F0 - dr^2 F-) / (dl dr (dl+dr))
+        r.c1p = dl / (dr * (dl + dr));
+        r.c10 = (dr - dl) / (dl * dr);
+        r.c1m = -dr / (dl * (dl + dr));
+        // Eq. (nonphi2): 2 (dl F+ - (dl+dr) F0 + dr F-) / (dl dr (dl+dr))
+        r.c2p = 2.0 / (dr * (dl + dr));
+        r.c20 = -2.0 / (dl * dr);
+        r.c2m = 2.0 / (dl * (dl + dr));
+        if (has_m && has_p) { r.e1m = r.c1m; r.e10 = r.c10; r.e1p = r.c1p; }
+        else if (has_p) { r.e1m = 0.0; r.e10 = -1.0 / dr; r.e1p = 1.0 / dr; }
+        else if (has_m) { r.e1m = -1.0 / dl; r.e10 = 1.0 / dl; r.e1p = 0.0; }
+        else { r.e1m = r.e10 = r.e1p = 0.0; }
+        r.lo_wall = (wall && k == 0) ? 1 : 0;
+        r.hi_wall = (wall && k == n - 1) ? 1 : 0;
+        if (!r.hi_wall) {
+            const double hL = 0.5 * d[k], hR = 0.5 * d[kp];
+            r.wL = hR / (hL + hR);
+            r.wR = hL / (hL + hR);
+            r.invd = 1.0 / (hL + hR);
+        }
+        out.push_back(r);
+    }
+}
+
+template <typename T>
+Planes<T> &planes(dugks_sim *s);
+template <>
+Planes<double> &planes<double>(dugks_sim *s) { return s->P64; }
+template <>
+Planes<float> &planes<float>(dugks_sim *s) { return s->P32; }
+
+cudaEvent_t take_event(dugks_sim *s)
+{
+    if (!s->ev_pool.empty()) {
+        cudaEvent_t e = s->ev_pool.back();
+        s->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Bracket one launch with events when timing is on.
+struct Timed {
+    dugks_sim *s;
+    int k;
+    cudaEvent_t a = nullptr, b = nullptr;
+    Timed(dugks_sim *s_, int k_) : s(s_), k(k_)
+    {
+        s->launches++;
+        if (s->timing && k >= 0) {
+            a = take_event(s);
+            b = take_event(s);
+            cudaEventRecord(a, s->stream);
+        }
+    }
+    ~Timed()
+    {
+        if (a) {
+            cudaEventRecord(b, s->stream);
+            s->ev_used.push_back({a, b, k});
+        }
+    }
+};
+
+void harvest_events(dugks_sim *s)
+{
+    for (auto &e : s->ev_used) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
+            s->k_ms[e.kernel] += ms;
+            s->k_n[e.kernel] += 1;
+        }
+        s->ev_pool.push_back(e.a);
+        s->ev_pool.push_back(e.b);
+    }
+    s->ev_used.clear();
+}
+
+template <typename T>
+int launch_step(dugks_sim *s)
+{
+    Planes<T> &P = planes<T>(s);
+    const dim3 blk(TX, TY);
+    const unsigned g = (unsigned)s->n_tiles;
+    { Timed t(s, K_MU); k_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P); }
+    { Timed t(s, K_MACRO); k_macro<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, 0); }
+    { Timed t(s, K_CELL); k_cell<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P); }
+    { Timed t(s, K_FACE); k_face<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P); }
+    return cuda_status(cudaGetLastError());
+}
+
+template <typename T>
+int do_init(dugks_sim *s)
+{
+    Planes<T> &P = planes<T>(s);
+    const dim3 blk(TX, TY);
+    const unsigned g = (unsigned)s->n_tiles;
+    const long long D = s->n_dense;
+    { Timed t(s, -1); k_unpack<double><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_stage + 0 * D, P.phi, s->d_dense0); }
+    { Timed t(s, -1); k_unpack<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_stage + 1 * D, P.ux, s->d_dense0); }
+    { Timed t(s, -1); k_unpack<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_stage + 2 * D, P.uy, s->d_dense0); }
+    { Timed t(s, -1); k_unpack<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_stage + 3 * D, P.p, s->d_dense0); }
+    { Timed t(s, K_MU); k_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P); }
+    { Timed t(s, K_INIT); k_init<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P); }
+    // FP64: phi = sum g of the new state, as the next step recomputes it; FP32:
+    // the given phi stays the authoritative FP64 order parameter
+    if (sizeof(T) == sizeof(double)) { Timed t(s, -1); k_phi<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, P); }
+    return cuda_status(cudaGetLastError());
+}
+
+template <typename T>
+int do_moments(dugks_sim *s)
+{
+    Planes<T> &P = planes<T>(s);
+    const dim3 blk(TX, TY);
+    const unsigned g = (unsigned)s->n_tiles;
+    const long long D = s->n_dense;
+    { Timed t(s, K_MU); k_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P); }
+    { Timed t(s, K_MACRO); k_macro<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, 1); }
+    { Timed t(s, -1); k_pack<double><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, P.phi, s->d_stage, s->d_dense0); }
+    T *src[4] = {P.rho, P.ux, P.uy, P.p};
+    for (int k = 0; k < 4; k++) {
+        Timed t(s, -1);
+        k_pack<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, src[k], s->d_stage + (k + 1) * D, s->d_dense0);
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+template <typename T>
+int do_pack_state(dugks_sim *s, double *dst_dev)
+{
+    Planes<T> &P = planes<T>(s);
+    const dim3 blk(TX, TY);
+    const unsigned g = (unsigned)s->n_tiles;
+    for (int q = 0; q < 2 * Q; q++) {
+        const T *src = (q < Q ? P.f : P.g) + (long long)(q % Q) * P.N;
+        Timed t(s, -1);
+        k_pack<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, src, dst_dev + (long long)q * s->n_dense, s->d_dense0);
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+template <typename T>
+int do_unpack_state(dugks_sim *s, const double *src_dev)
+{
+    Planes<T> &P = planes<T>(s);
+    const dim3 blk(TX, TY);
+    const unsigned g = (unsigned)s->n_tiles;
+    for (int q = 0; q < 2 * Q; q++) {
+        T *dst = (q < Q ? P.f : P.g) + (long long)(q % Q) * P.N;
+        Timed t(s, -1);
+        k_unpack<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, src_dev + (long long)q * s->n_dense, dst, s->d_dense0);
+    }
+    { Timed t(s, -1); k_phi<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, P); }
+    return cuda_status(cudaGetLastError());
+}
+
+template <typename T>
+int do_reduce(dugks_sim *s)
+{
+    Planes<T> &P = planes<T>(s);
+    const dim3 blk(TX, TY);
+    { Timed t(s, K_REDUCE); k_reduce<T><<<(unsigned)s->n_tiles, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, s->d_partials); }
+    { Timed t(s, -1); k_reduce_inst<<<(s->n_inst + 127) / 128, 128, 0, s->stream>>>(s->d_inst, s->n_inst, s->d_partials, s->d_sums); }
+    return cuda_status(cudaGetLastError());
+}
+
+template <typename T>
+void assign_planes(dugks_sim *s, Planes<T> &P, T *base)
+{
+    const long long N = s->N;
+    T *p = base;
+    P.f = p; p += Q * N;
+    P.g = p; p += Q * N;
+    P.fbp = p; p += Q * N;
+    P.gbp = p; p += Q * N;
+    T **one[] = {&P.mu, &P.lapmu, &P.gmux, &P.gmuy, &P.gphix, &P.gphiy, &P.p, &P.ux, &P.uy, &P.gpx, &P.gpy, &P.rho};
+    for (T **q : one) { *q = p; p += N; }
+    P.phi = s->d_phi;
+    P.N = N;
+    P.status = s->d_status;
+}
+
+constexpr int kNumScalarPlanes = 12;
+
+void free_sim(dugks_sim *s)
+{
+    if (!s) return;
+    cudaFree(s->d_inst);
+    cudaFree(s->d_tiles);
+    cudaFree(s->d_geo);
+    cudaFree(s->d_dense0);
+    cudaFree(s->d_planes);
+    cudaFree(s->d_phi);
+    cudaFree(s->d_status);
+    cudaFree(s->d_partials);
+    cudaFree(s->d_sums);
+    cudaFree(s->d_stage);
+    for (auto &e : s->ev_used) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
+    for (auto e : s->ev_pool) cudaEventDestroy(e);
+    delete s;
+}
+
+// After a synchronisation: a single simulation reports a non-finite state as
+// DUGKS_ERR_NONFINITE; a batch masks the affected instances and reports them
+// through dugks_batch_status only.
+int sync_status(dugks_sim *s)
+{
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (s->n_inst > 1) return DUGKS_OK;
+    std::vector<int> st(s->n_inst);
+    e = cudaMemcpy(st.data(), s->d_status, sizeof(int) * s->n_inst, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int v : st) if (v) return DUGKS_ERR_NONFINITE;
+    return DUGKS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *params, void *cuda_stream, dugks_sim **out)
+{
+    if (!out) return DUGKS_ERR_ARG;
+    *out = nullptr;
+    if (n < 1 || !meshes || !params) return DUGKS_ERR_ARG;
+    for (int k = 0; k < n; k++) {
+        int rc = validate(meshes[k], params[k]);
+        if (rc) return rc;
+        if (params[k].precision != params[0].precision) return DUGKS_ERR_ARG;
+    }
+    dugks_sim *s = new (std::nothrow) dugks_sim();
+    if (!s) return DUGKS_ERR_OOM;
+    s->n_inst = n;
+    s->prec = params[0].precision;
+    s->stream = (cudaStream_t)cuda_stream;
+    std::vector<AxisRec> geo;
+    std::vector<int4> tiles;
+    long long cell = 0, dense = 0;
+    for (int k = 0; k < n; k++) {
+        const dugks_mesh &m = meshes[k];
+        const dugks_params &p = params[k];
+        InstDev I;
+        std::memset(&I, 0, sizeof(I));
+        I.nx = m.nx;
+        I.ny = m.ny;
+        I.nxp = (m.nx + 31) / 32 * 32;
+        I.bcx = m.bc_x;
+        I.bcy = m.bc_y;
+        I.cell0 = cell;
+        cell += (long long)I.nxp * m.ny;
+        s->h_dense0.push_back(dense);
+        dense += (long long)m.nx * m.ny;
+        I.gx_off = (long long)geo.size();
+        axis_records(m.nx, m.dx, m.bc_x, geo);
+        I.gy_off = (long long)geo.size();
+        axis_records(m.ny, m.dy, m.bc_y, geo);
+        I.phiA = p.phiA; I.phiB = p.phiB; I.rhoA = p.rhoA; I.rhoB = p.rhoB;
+        I.muA = p.rhoA * p.nuA;
+        I.muB = p.rhoB * p.nuB;
+        I.lambda = p.mobility; I.tau_g = p.tau_g; I.beta = p.beta; I.kappa = p.kappa;
+        I.gxa = p.gx; I.gya = p.gy; I.rho_ref = p.rho_ref;
+        double dmin = m.dx[0];
+        for (int i = 0; i < m.nx; i++) dmin = std::min(dmin, m.dx[i]);
+        for (int j = 0; j < m.ny; j++) dmin = std::min(dmin, m.dy[j]);
+        I.dt = p.cfl * dmin / std::sqrt(2.0);          // Eq. (cfl), C_max = sqrt(6 RT) = sqrt(2)
+        I.h = 0.5 * I.dt;
+        I.eta = p.mobility / (p.tau_g / 3.0);           // Eq. (kineticandmobility)
+        const double rr = p.rhoA / p.rhoB;
+        I.gamma = (rr - 1.0) / (p.phiA - p.phiB * rr);  // Eq. (Gama)
+        I.drho = (p.rhoA - p.rhoB) / (p.phiA - p.phiB); // Eq. (oderrho)
+        I.tile0 = (int)tiles.size();
+        for (int ty = 0; ty < m.ny; ty += TY)
+            for (int tx = 0; tx < m.nx; tx += TX) tiles.push_back(make_int4(k, tx, ty, 0));
+        I.ntiles = (int)tiles.size() - I.tile0;
+        s->h_inst.push_back(I);
+    }
+    s->N = cell;
+    s->n_dense = dense;
+    s->n_tiles = (int)tiles.size();
+    const size_t esz = s->prec == DUGKS_FP64 ? sizeof(double) : sizeof(float);
+    const size_t plane_elems = (size_t)(4 * Q + kNumScalarPlanes) * (size_t)s->N;
+    cudaError_t e = cudaSuccess;
+    auto chk = [&](cudaError_t r) { if (r != cudaSuccess && e == cudaSuccess) e = r; };
+    chk(cudaMalloc(&s->d_inst, sizeof(InstDev) * n));
+    chk(cudaMalloc(&s->d_tiles, sizeof(int4) * tiles.size()));
+    chk(cudaMalloc(&s->d_geo, sizeof(AxisRec) * geo.size()));
+    chk(cudaMalloc(&s->d_dense0, sizeof(long long) * n));
+    chk(cudaMalloc(&s->d_planes, esz * plane_elems));
+    chk(cudaMalloc(&s->d_phi, sizeof(double) * (size_t)s->N));
+    chk(cudaMalloc(&s->d_status, sizeof(int) * n));
+    chk(cudaMalloc(&s->d_partials, sizeof(double2) * tiles.size()));
+    chk(cudaMalloc(&s->d_sums, sizeof(double2) * n));
+    chk(cudaMalloc(&s->d_stage, sizeof(double) * (size_t)std::max<long long>(5, 2 * Q) * (size_t)dense));
+    if (e != cudaSuccess) {
+        int rc = cuda_status(e);
+        free_sim(s);
+        return rc;
+    }
+    chk(cudaMemcpy(s->d_inst, s->h_inst.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice));
+    chk(cudaMemcpy(s->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice));
+    chk(cudaMemcpy(s->d_geo, geo.data(), sizeof(AxisRec) * geo.size(), cudaMemcpyHostToDevice));
+    chk(cudaMemcpy(s->d_dense0, s->h_dense0.data(), sizeof(long long) * n, cudaMemcpyHostToDevice));
+    chk(cudaMemset(s->d_planes, 0, esz * plane_elems));
+    chk(cudaMemset(s->d_phi, 0, sizeof(double) * (size_t)s->N));
+    chk(cudaMemset(s->d_status, 0, sizeof(int) * n));
+    if (e != cudaSuccess) {
+        int rc = cuda_status(e);
+        free_sim(s);
+        return rc;
+    }
+    if (s->prec == DUGKS_FP64) assign_planes<double>(s, s->P64, (double *)s->d_planes);
+    else assign_planes<float>(s, s->P32, (float *)s->d_planes);
+    *out = s;
+    return DUGKS_OK;
+}
+
+int dugks_create(const dugks_mesh *mesh, const dugks_params *params, void *cuda_stream, dugks_sim **out)
+{
+    return dugks_batch_create(1, mesh, params, cuda_stream, out);
+}
+
+void dugks_destroy(dugks_sim *sim)
+{
+    if (!sim) return;
+    cudaStreamSynchronize(sim->stream);
+    free_sim(sim);
+}
+
+int dugks_init(dugks_sim *s, const double *phi, const double *ux, const double *uy, const double *p)
+{
+    if (!s || !phi) return DUGKS_ERR_ARG;
+    const long long D = s->n_dense;
+    for (long long c = 0; c < D; c++) if (!std::isfinite(phi[c])) return DUGKS_ERR_NONFINITE;
+    const double *src[4] = {phi, ux, uy, p};
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 4 && e == cudaSuccess; k++) {
+        if (src[k]) e = cudaMemcpyAsync(s->d_stage + k * D, src[k], sizeof(double) * D, cudaMemcpyHostToDevice, s->stream);
+        else e = cudaMemsetAsync(s->d_stage + k * D, 0, sizeof(double) * D, s->stream);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_status, 0, sizeof(int) * s->n_inst, s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    int rc = s->prec == DUGKS_FP64 ? do_init<double>(s) : do_init<float>(s);
+    if (rc) return rc;
+    return sync_status(s);
+}
+
+int dugks_step(dugks_sim *s, long nsteps)
+{
+    if (!s || nsteps < 0) return DUGKS_ERR_ARG;
+    for (long k = 0; k < nsteps; k++) {
+        int rc = s->prec == DUGKS_FP64 ? launch_step<double>(s) : launch_step<float>(s);
+        if (rc) return rc;
+    }
+    return DUGKS_OK;
+}
+
+int dugks_moments(dugks_sim *s, double *phi, double *rho, double *ux, double *uy, double *p)
+{
+    if (!s) return DUGKS_ERR_ARG;
+    int rc = s->prec == DUGKS_FP64 ? do_moments<double>(s) : do_moments<float>(s);
+    if (rc) return rc;
+    const long long D = s->n_dense;
+    double *dst[5] = {phi, rho, ux, uy, p};
+    for (int k = 0; k < 5; k++) {
+        if (!dst[k]) continue;
+        cudaError_t e = cudaMemcpyAsync(dst[k], s->d_stage + k * D, sizeof(double) * D, cudaMemcpyDeviceToHost, s->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return sync_status(s);
+}
+
+int dugks_conservation(dugks_sim *s, double *sum_phi, double *sum_rho)
+{
+    if (!s) return DUGKS_ERR_ARG;
+    int rc = s->prec == DUGKS_FP64 ? do_reduce<double>(s) : do_reduce<float>(s);
+    if (rc) return rc;
+    std::vector<double2> h(s->n_inst);
+    cudaError_t e = cudaMemcpyAsync(h.data(), s->d_sums, sizeof(double2) * s->n_inst, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int k = 0; k < s->n_inst; k++) {
+        if (sum_phi) sum_phi[k] = h[k].x;
+        if (sum_rho) sum_rho[k] = h[k].y;
+    }
+    return sync_status(s);
+}
+
+int dugks_batch_status(dugks_sim *s, int *per_instance_status)
+{
+    if (!s || !per_instance_status) return DUGKS_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    std::vector<int> st(s->n_inst);
+    e = cudaMemcpy(st.data(), s->d_status, sizeof(int) * s->n_inst, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int k = 0; k < s->n_inst; k++) per_instance_status[k] = st[k] ? DUGKS_ERR_NONFINITE : DUGKS_OK;
+    return DUGKS_OK;
+}
+
+int dugks_dt(const dugks_sim *s, int instance, double *dt)
+{
+    if (!s || !dt || instance < 0 || instance >= s->n_inst) return DUGKS_ERR_ARG;
+    *dt = s->h_inst[instance].dt;
+    return DUGKS_OK;
+}
+
+int dugks_info(const dugks_sim *s, int *n_instances, long *n_cells, size_t *state_bytes)
+{
+    if (!s) return DUGKS_ERR_ARG;
+    if (n_instances) *n_instances = s->n_inst;
+    if (n_cells) *n_cells = (long)s->n_dense;
+    if (state_bytes) *state_bytes = (size_t)2 * Q * (size_t)s->n_dense * (s->prec == DUGKS_FP64 ? 8 : 4);
+    return DUGKS_OK;
+}
+
+int dugks_save(dugks_sim *s, void *buf, size_t *bytes)
+{
+    if (!s || !bytes) return DUGKS_ERR_ARG;
+    const size_t need = sizeof(double) * 2 * Q * (size_t)s->n_dense;
+    if (!buf) { *bytes = need; return DUGKS_OK; }
+    if (*bytes < need) return DUGKS_ERR_ARG;
+    int rc = s->prec == DUGKS_FP64 ? do_pack_state<double>(s, s->d_stage) : do_pack_state<float>(s, s->d_stage);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(buf, s->d_stage, need, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    *bytes = need;
+    return DUGKS_OK;
+}
+
+int dugks_load(dugks_sim *s, const void *buf, size_t bytes)
+{
+    if (!s || !buf) return DUGKS_ERR_ARG;
+    const size_t need = sizeof(double) * 2 * Q * (size_t)s->n_dense;
+    if (bytes != need) return DUGKS_ERR_ARG;
+    const double *h = (const double *)buf;
+    for (size_t k = 0; k < need / sizeof(double); k++) if (!std::isfinite(h[k])) return DUGKS_ERR_NONFINITE;
+    cudaError_t e = cudaMemcpyAsync(s->d_stage, buf, need, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_status, 0, sizeof(int) * s->n_inst, s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    int rc = s->prec == DUGKS_FP64 ? do_unpack_state<double>(s, s->d_stage) : do_unpack_state<float>(s, s->d_stage);
+    if (rc) return rc;
+    return sync_status(s);
+}
+
+int dugks_launch_count(const dugks_sim *s, long *count)
+{
+    if (!s || !count) return DUGKS_ERR_ARG;
+    *count = s->launches;
+    return DUGKS_OK;
+}
+
+int dugks_set_timing(dugks_sim *s, int enable)
+{
+    if (!s) return DUGKS_ERR_ARG;
+    s->timing = enable != 0;
+    return DUGKS_OK;
+}
+
+int dugks_kernel_times(dugks_sim *s, double *ms, long *launches)
+{
+    if (!s) return DUGKS_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    harvest_events(s);
+    for (int k = 0; k < K_COUNT; k++) {
+        if (ms) ms[k] = s->k_ms[k];
+        if (launches) launches[k] = s->k_n[k];
+        s->k_ms[k] = 0.0;
+        s->k_n[k] = 0;
+    }
+    return DUGKS_OK;
+}
+
+const char *dugks_kernel_name(int k)
+{
+    if (k < 0 || k >= K_COUNT) return "?";
+    return kNames[k];
+}
+
+int dugks_kernel_bytes_per_cell(const dugks_sim *s, int k, double *bytes)
+{
+    if (!s || !bytes || k < 0 || k >= K_COUNT) return DUGKS_ERR_ARG;
+    // Compulsory bytes per cell of one launch: each plane a kernel reads or
+    // writes counted once (halo re-reads excluded).  w = distribution/aux word,
+    // the order parameter plane is FP64 in both precisions.
+    const bool f64 = s->prec == DUGKS_FP64;
+    const double w = f64 ? 8.0 : 4.0;
+    double b = 0.0;
+    switch (k) {
+    case K_MU: b = 8 + w; break;                                   // phi -> mu
+    case K_MACRO: b = 8 + (1 + 9) * w + 8 * w; break;              // phi, mu, f -> 8 planes
+    case K_CELL: b = 8 + (1 + 9 + 9 + 8) * w + 20 * w; break;      // phi, p, f, g, 8 planes -> grad p, bar-plus
+    case K_FACE: b = (18 + 8 + 18 + 18) * w + (f64 ? 8 : 16); break; // bar-plus, aux, tilde r/w, phi
+    case K_INIT: b = 8 + 4 * w + 18 * w; break;
+    case K_REDUCE: b = 8; break;
+    }
+    *bytes = b;
+    return DUGKS_OK;
+}
+
+const char *dugks_status_str(int st)
+{
+    switch (st) {
+    case DUGKS_OK: return "ok";
+    case DUGKS_ERR_ARG: return "invalid argument";
+    case DUGKS_ERR_CUDA: return "CUDA error";
+    case DUGKS_ERR_NONFINITE: return "non-finite state";
+    case DUGKS_ERR_OOM: return "out of device memory";
+    case DUGKS_ERR_TIMEOUT: return "device wait timed out";
+    case DUGKS_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,617 @@
+// dugks_kernels.cuh -- CUDA kernels of one two-phase DUGKS step (sm_103a).
+//
+// One step of the procedure of Sec. 2.2 runs as four launches over a table of
+// 32x8-cell tiles that covers every instance of a batch:
+//   k_mu    : mu = psi'(phi) - kappa lap(phi)                    (Eq. chemicalpotential)
+//   k_macro : grad mu, lap mu, grad phi, F, u, p                  (Eqs. u, P)
+//   k_cell  : grad p, tau_f, equilibria, sources, bar-plus        (Eqs. feq, geq, F, G, relations1)
+//   k_face  : face reconstruction, face macros, originals, flux,
+//             tilde update in place, phi = sum g for the next step (Eqs. fbar_h, original-function,
+//                                                                   microfluxf, updatef, relations2)
+// plus k_init (step 1) and k_reduce (FP64 conservation sums).
+#pragma once
+#include "dugks_common.cuh"
+
+namespace dugks {
+
+template <typename T>
+struct Cst {
+    static constexpr T cs2 = T(1.0 / 3.0);   // c_s^2 = RT = 1/3
+    static constexpr T half = T(0.5);
+};
+
+__device__ __forceinline__ long long cell_of(const InstDev &I, int i, int j)
+{
+    return I.cell0 + (long long)j * I.nxp + i;
+}
+
+template <typename T>
+__device__ __forceinline__ T rho_of(const InstDev &I, T phi)
+{
+    // Eq. (oderrho) written as rhoB + (rhoA - rhoB)(phi - phiB)/(phiA - phiB)
+    return T(I.rhoB) + T(I.drho) * (phi - T(I.phiB));
+}
+
+template <typename T>
+__device__ __forceinline__ T tauf_of(const InstDev &I, T phi, T rho)
+{
+    // Eq. (mixvis) and tau_f = nu / c_s^2 with nu = mu / rho (Eq. kineticandmobility)
+    T muA = T(I.muA), muB = T(I.muB);
+    T mu = muA * muB * (T(I.phiA) - T(I.phiB)) / ((phi - T(I.phiB)) * muB + (T(I.phiA) - phi) * muA);
+    return mu / (rho * Cst<T>::cs2);
+}
+
+// s_i(u) of Eq. (su)
+template <typename T>
+__device__ __forceinline__ T s_of(int q, T ux, T uy)
+{
+    T xu = T(cx(q)) * ux + T(cy(q)) * uy;
+    T uu = ux * ux + uy * uy;
+    const T cs2 = Cst<T>::cs2;
+    return T(wq(q)) * (xu / cs2 + xu * xu / (T(2) * cs2 * cs2) - uu / (T(2) * cs2));
+}
+
+// Point state from which equilibria and sources follow.
+template <typename T>
+struct Pt {
+    T phi, rho, ux, uy, p, mu, lapmu, Fx, Fy, grx, gry, gpx, gpy, tauf;
+};
+
+// f^eq_q, g^eq_q (Eqs. feq, geq, Hi) and F^f_q, F^g_q (Eqs. F, G)
+template <typename T>
+__device__ __forceinline__ void eq_src(const InstDev &I, const Pt<T> &s, int q, T &feq, T &geq, T &Ff, T &Fg)
+{
+    const T cs2 = Cst<T>::cs2;
+    T si = s_of<T>(q, s.ux, s.uy);
+    T w = T(wq(q));
+    T emu = T(I.eta) * s.mu;
+    feq = w * s.p + cs2 * s.rho * si;
+    T H = (q == 0) ? s.phi - (T(1) - w) * emu : w * emu;
+    geq = H + s.phi * si;
+    T G = w + si;
+    T ex = T(cx(q)) - s.ux, ey = T(cy(q)) - s.uy;
+    Ff = ex * (s.Fx * G + si * cs2 * s.grx) + ey * (s.Fy * G + si * cs2 * s.gry)
+       - w * cs2 * s.rho * T(I.gamma) * T(I.lambda) * s.lapmu;
+    Fg = s.phi / (cs2 * s.rho) * (ex * (s.Fx - s.gpx) + ey * (s.Fy - s.gpy)) * G;
+}
+
+// ---------------------------------------------------------------------------
+// k_mu: chemical potential (Eq. chemicalpotential) with the 5-point Laplacian
+// of Eq. (nonphi2) on both axes.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(TX *TY) k_mu(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles,
+                                               const AxisRec *__restrict__ geo, Planes<T> P)
+{
+    const int4 t = tiles[blockIdx.x];
+    const InstDev &I = insts[t.x];
+    if (P.status[t.x]) return;   // masked: non-finite instance of a batch
+    const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
+    if (i >= I.nx || j >= I.ny) return;
+    const AxisRec &ax = geo[I.gx_off + i];
+    const AxisRec &ay = geo[I.gy_off + j];
+    const long long c = cell_of(I, i, j);
+    // Differences are formed in FP64 and only then rounded to T, so that the
+    // Laplacian of the FP64 order parameter keeps its precision in FP32 mode
+    // (the stencil weights sum to zero: c2m + c20 + c2p = 0).
+    const double p0 = P.phi[c];
+    T lap = (T(ax.c2m) * T(P.phi[cell_of(I, ax.km, j)] - p0) + T(ax.c2p) * T(P.phi[cell_of(I, ax.kp, j)] - p0))
+          + (T(ay.c2m) * T(P.phi[cell_of(I, i, ay.km)] - p0) + T(ay.c2p) * T(P.phi[cell_of(I, i, ay.kp)] - p0));
+    T dpsi = T(4) * T(I.beta) * T(p0 - I.phiA) * T(p0 - I.phiB) * T(p0 - 0.5 * (I.phiA + I.phiB));
+    P.mu[c] = dpsi - T(I.kappa) * lap;
+}
+
+// first derivatives of a cell field along x and y (mirror ghosts)
+template <typename T>
+__device__ __forceinline__ void grad_field(const InstDev &I, const T *__restrict__ F, const AxisRec &ax,
+                                           const AxisRec &ay, int i, int j, T f0, T &gx, T &gy)
+{
+    gx = T(ax.c1m) * F[cell_of(I, ax.km, j)] + T(ax.c10) * f0 + T(ax.c1p) * F[cell_of(I, ax.kp, j)];
+    gy = T(ay.c1m) * F[cell_of(I, i, ay.km)] + T(ay.c10) * f0 + T(ay.c1p) * F[cell_of(I, i, ay.kp)];
+}
+
+// first derivatives of the FP64 order parameter, difference form (weights sum to zero)
+template <typename T>
+__device__ __forceinline__ void grad_phi(const InstDev &I, const double *__restrict__ F, const AxisRec &ax,
+                                         const AxisRec &ay, int i, int j, double f0, T &gx, T &gy)
+{
+    gx = T(ax.c1m) * T(F[cell_of(I, ax.km, j)] - f0) + T(ax.c1p) * T(F[cell_of(I, ax.kp, j)] - f0);
+    gy = T(ay.c1m) * T(F[cell_of(I, i, ay.km)] - f0) + T(ay.c1p) * T(F[cell_of(I, i, ay.kp)] - f0);
+}
+
+// ---------------------------------------------------------------------------
+// k_macro: grad mu, lap mu, grad phi, total force F = -phi grad mu + F_b, and
+// Eqs. (u), (P) from the tracked f.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(TX *TY) k_macro(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles,
+                                                  const AxisRec *__restrict__ geo, Planes<T> P, int write_rho)
+{
+    const int4 t = tiles[blockIdx.x];
+    const InstDev &I = insts[t.x];
+    if (P.status[t.x]) return;   // masked: non-finite instance of a batch
+    const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
+    if (i >= I.nx || j >= I.ny) return;
+    const AxisRec &ax = geo[I.gx_off + i];
+    const AxisRec &ay = geo[I.gy_off + j];
+    const long long c = cell_of(I, i, j);
+    const long long N = P.N;
+    const T cs2 = Cst<T>::cs2;
+    const T phi = T(P.phi[c]), mu = P.mu[c];
+    T gmx, gmy, gfx, gfy;
+    grad_field(I, P.mu, ax, ay, i, j, mu, gmx, gmy);
+    grad_phi(I, P.phi, ax, ay, i, j, P.phi[c], gfx, gfy);
+    T lmu = (T(ax.c2m) * P.mu[cell_of(I, ax.km, j)] + T(ax.c20) * mu + T(ax.c2p) * P.mu[cell_of(I, ax.kp, j)])
+          + (T(ay.c2m) * P.mu[cell_of(I, i, ay.km)] + T(ay.c20) * mu + T(ay.c2p) * P.mu[cell_of(I, i, ay.kp)]);
+    T rho = rho_of<T>(I, phi);
+    T Fx = -phi * gmx + (rho - T(I.rho_ref)) * T(I.gxa);
+    T Fy = -phi * gmy + (rho - T(I.rho_ref)) * T(I.gya);
+    T sf = 0, mx = 0, my = 0;
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+        T v = P.f[q * N + c];
+        sf += v;
+        if (cx(q)) mx += T(cx(q)) * v;
+        if (cy(q)) my += T(cy(q)) * v;
+    }
+    T hdt = T(0.5) * T(I.dt);
+    T ux = (mx + hdt * cs2 * Fx) / (cs2 * rho);
+    T uy = (my + hdt * cs2 * Fy) / (cs2 * rho);
+    T grx = T(I.drho) * gfx, gry = T(I.drho) * gfy;
+    T p = sf + hdt * cs2 * (ux * grx + uy * gry - T(I.gamma) * rho * T(I.lambda) * lmu);
+    P.gmux[c] = gmx;
+    P.gmuy[c] = gmy;
+    P.lapmu[c] = lmu;
+    P.gphix[c] = gfx;
+    P.gphiy[c] = gfy;
+    P.ux[c] = ux;
+    P.uy[c] = uy;
+    P.p[c] = p;
+    if (write_rho) P.rho[c] = rho;
+}
+
+template <typename T>
+__device__ __forceinline__ void cell_point(const InstDev &I, const Planes<T> &P, long long c, T gpx, T gpy, Pt<T> &s)
+{
+    s.phi = T(P.phi[c]);
+    s.rho = rho_of<T>(I, s.phi);
+    s.ux = P.ux[c];
+    s.uy = P.uy[c];
+    s.p = P.p[c];
+    s.mu = P.mu[c];
+    s.lapmu = P.lapmu[c];
+    T gmx = P.gmux[c], gmy = P.gmuy[c];
+    s.Fx = -s.phi * gmx + (s.rho - T(I.rho_ref)) * T(I.gxa);
+    s.Fy = -s.phi * gmy + (s.rho - T(I.rho_ref)) * T(I.gya);
+    s.grx = T(I.drho) * P.gphix[c];
+    s.gry = T(I.drho) * P.gphiy[c];
+    s.gpx = gpx;
+    s.gpy = gpy;
+    s.tauf = tauf_of<T>(I, s.phi, s.rho);
+}
+
+// ---------------------------------------------------------------------------
+// k_cell: grad p, then bar-plus of both distributions at the cell centre
+// (step 2, Eq. relations1).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(TX *TY) k_cell(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles,
+                                                 const AxisRec *__restrict__ geo, Planes<T> P)
+{
+    const int4 t = tiles[blockIdx.x];
+    const InstDev &I = insts[t.x];
+    if (P.status[t.x]) return;   // masked: non-finite instance of a batch
+    const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
+    if (i >= I.nx || j >= I.ny) return;
+    const AxisRec &ax = geo[I.gx_off + i];
+    const AxisRec &ay = geo[I.gy_off + j];
+    const long long c = cell_of(I, i, j);
+    const long long N = P.N;
+    T gpx, gpy;
+    grad_field(I, P.p, ax, ay, i, j, P.p[c], gpx, gpy);
+    P.gpx[c] = gpx;
+    P.gpy[c] = gpy;
+    Pt<T> s;
+    cell_point(I, P, c, gpx, gpy, s);
+    const T dt = T(I.dt), h = T(I.h), tg = T(I.tau_g), tf = s.tauf;
+    // Eq. (relations1) coefficients
+    const T af = (T(2) * tf - h) / (T(2) * tf + dt), bf = T(3) * h / (T(2) * tf + dt), cf = T(3) * tf * h / (T(2) * tf + dt);
+    const T ag = (T(2) * tg - h) / (T(2) * tg + dt), bg = T(3) * h / (T(2) * tg + dt), cg = T(3) * tg * h / (T(2) * tg + dt);
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+        T feq, geq, Ff, Fg;
+        eq_src<T>(I, s, q, feq, geq, Ff, Fg);
+        P.fbp[q * N + c] = af * P.f[q * N + c] + bf * feq + cf * Ff;
+        P.gbp[q * N + c] = ag * P.g[q * N + c] + bg * geq + cg * Fg;
+    }
+}
+
+// Face macroscopic variables from the bar distributions at t+h (Eq.
+// conservedVariable with h and bar), then equilibria, sources and the original
+// distributions of Eq. (original-function) for every direction.
+template <typename T>
+struct FaceAux {
+    T mu, lapmu, gmux, gmuy, gpx, gpy, gphix, gphiy;
+};
+
+template <typename T>
+__device__ __forceinline__ void face_originals(const InstDev &I, const T (&fb)[Q], const T (&gb)[Q],
+                                               const FaceAux<T> &ax, bool wall, T (&fo)[Q], T (&go)[Q])
+{
+    const T cs2 = Cst<T>::cs2;
+    const T h = T(I.h);
+    T phi = 0, sf = 0, mx = 0, my = 0;
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+        phi += gb[q];
+        sf += fb[q];
+        if (cx(q)) mx += T(cx(q)) * fb[q];
+        if (cy(q)) my += T(cy(q)) * fb[q];
+    }
+    Pt<T> s;
+    s.phi = phi;
+    s.rho = rho_of<T>(I, phi);
+    s.Fx = -phi * ax.gmux + (s.rho - T(I.rho_ref)) * T(I.gxa);
+    s.Fy = -phi * ax.gmuy + (s.rho - T(I.rho_ref)) * T(I.gya);
+    s.grx = T(I.drho) * ax.gphix;
+    s.gry = T(I.drho) * ax.gphiy;
+    if (wall) {
+        s.ux = 0;
+        s.uy = 0;
+    } else {
+        s.ux = (mx + T(0.5) * h * cs2 * s.Fx) / (cs2 * s.rho);
+        s.uy = (my + T(0.5) * h * cs2 * s.Fy) / (cs2 * s.rho);
+    }
+    s.p = sf + T(0.5) * h * cs2 * (s.ux * s.grx + s.uy * s.gry - T(I.gamma) * s.rho * T(I.lambda) * ax.lapmu);
+    s.mu = ax.mu;
+    s.lapmu = ax.lapmu;
+    s.gpx = ax.gpx;
+    s.gpy = ax.gpy;
+    s.tauf = tauf_of<T>(I, phi, s.rho);
+    const T tf = s.tauf, tg = T(I.tau_g);
+    const T a1 = T(2) * tf / (T(2) * tf + h), b1 = h / (T(2) * tf + h), c1 = tf * h / (T(2) * tf + h);
+    const T a2 = T(2) * tg / (T(2) * tg + h), b2 = h / (T(2) * tg + h), c2 = tg * h / (T(2) * tg + h);
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+        T feq, geq, Ff, Fg;
+        eq_src<T>(I, s, q, feq, geq, Ff, Fg);
+        fo[q] = a1 * fb[q] + b1 * feq + c1 * Ff;
+        go[q] = a2 * gb[q] + b2 * geq + c2 * Fg;
+    }
+}
+
+// Interior (or periodic) face on axis A between cell L = (iL, jL) and the next
+// cell R = (iR, jR); returns the original distributions at the face (steps 3-4).
+template <typename T, int A>
+__device__ void interior_face(const InstDev &I, const Planes<T> &P, const AxisRec *__restrict__ geo, int iL, int jL,
+                              int iR, int jR, T (&fo)[Q], T (&go)[Q])
+{
+    const long long N = P.N;
+    const AxisRec &rn = (A == 0) ? geo[I.gx_off + iL] : geo[I.gy_off + jL];
+    const AxisRec &rt = (A == 0) ? geo[I.gy_off + jL] : geo[I.gx_off + iL];
+    const T wL = T(rn.wL), wR = T(rn.wR), invd = T(rn.invd);
+    const T em = T(rt.e1m), e0 = T(rt.e10), ep = T(rt.e1p);
+    const long long cL = cell_of(I, iL, jL), cR = cell_of(I, iR, jR);
+    long long cLm, cLp, cRm, cRp;
+    if (A == 0) {
+        cLm = cell_of(I, iL, rt.km); cLp = cell_of(I, iL, rt.kp);
+        cRm = cell_of(I, iR, rt.km); cRp = cell_of(I, iR, rt.kp);
+    } else {
+        cLm = cell_of(I, rt.km, jL); cLp = cell_of(I, rt.kp, jL);
+        cRm = cell_of(I, rt.km, jR); cRp = cell_of(I, rt.kp, jR);
+    }
+    const T h = T(I.h);
+    T fb[Q], gb[Q];
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+        const T *Pf = P.fbp + q * N;
+        const T *Pg = P.gbp + q * N;
+        T bL = Pf[cL], bR = Pf[cR];
+        T tL = em * Pf[cLm] + e0 * bL + ep * Pf[cLp];
+        T tR = em * Pf[cRm] + e0 * bR + ep * Pf[cRp];
+        fb[q] = (wL * bL + wR * bR) - h * (T(ca(q, A)) * ((bR - bL) * invd) + T(ca(q, 1 - A)) * (wL * tL + wR * tR));
+        bL = Pg[cL]; bR = Pg[cR];
+        tL = em * Pg[cLm] + e0 * bL + ep * Pg[cLp];
+        tR = em * Pg[cRm] + e0 * bR + ep * Pg[cRp];
+        gb[q] = (wL * bL + wR * bR) - h * (T(ca(q, A)) * ((bR - bL) * invd) + T(ca(q, 1 - A)) * (wL * tL + wR * tR));
+    }
+    FaceAux<T> ax;
+    ax.mu = wL * P.mu[cL] + wR * P.mu[cR];
+    ax.lapmu = wL * P.lapmu[cL] + wR * P.lapmu[cR];
+    ax.gmux = wL * P.gmux[cL] + wR * P.gmux[cR];
+    ax.gmuy = wL * P.gmuy[cL] + wR * P.gmuy[cR];
+    ax.gpx = wL * P.gpx[cL] + wR * P.gpx[cR];
+    ax.gpy = wL * P.gpy[cL] + wR * P.gpy[cR];
+    ax.gphix = wL * P.gphix[cL] + wR * P.gphix[cR];
+    ax.gphiy = wL * P.gphiy[cL] + wR * P.gphiy[cR];
+    face_originals<T>(I, fb, gb, ax, false, fo, go);
+}
+
+// Wall face on axis A of cell (i, j), side = +1 (high end) or -1 (low end).
+// Outgoing and parallel bar distributions by Taylor reconstruction from the
+// cell centre, incoming ones by bounce-back; wall velocity zero; aux values
+// of the cell with zero normal gradient; incoming originals by bounce-back.
+template <typename T, int A>
+__device__ void wall_face(const InstDev &I, const Planes<T> &P, const AxisRec *__restrict__ geo, int i, int j,
+                          int side, T (&fo)[Q], T (&go)[Q])
+{
+    const long long N = P.N;
+    const AxisRec &rn = (A == 0) ? geo[I.gx_off + i] : geo[I.gy_off + j];
+    const AxisRec &rt = (A == 0) ? geo[I.gy_off + j] : geo[I.gx_off + i];
+    const long long c = cell_of(I, i, j);
+    long long cnm, cnp, ctm, ctp;
+    if (A == 0) {
+        cnm = cell_of(I, rn.km, j); cnp = cell_of(I, rn.kp, j);
+        ctm = cell_of(I, i, rt.km); ctp = cell_of(I, i, rt.kp);
+    } else {
+        cnm = cell_of(I, i, rn.km); cnp = cell_of(I, i, rn.kp);
+        ctm = cell_of(I, rt.km, j); ctp = cell_of(I, rt.kp, j);
+    }
+    const T h = T(I.h), half_d = T(0.5) * T(rn.d);
+    const T nm = T(rn.e1m), n0 = T(rn.e10), np = T(rn.e1p);
+    const T tm = T(rt.e1m), t0 = T(rt.e10), tp = T(rt.e1p);
+    T fb[Q], gb[Q];
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+        if (ca(q, A) * side < 0) continue;
+        const T *Pf = P.fbp + q * N;
+        const T *Pg = P.gbp + q * N;
+        const T off = T(side) * half_d - h * T(ca(q, A));
+        const T ht = h * T(ca(q, 1 - A));
+        T b = Pf[c];
+        fb[q] = b + off * (nm * Pf[cnm] + n0 * b + np * Pf[cnp]) - ht * (tm * Pf[ctm] + t0 * b + tp * Pf[ctp]);
+        b = Pg[c];
+        gb[q] = b + off * (nm * Pg[cnm] + n0 * b + np * Pg[cnp]) - ht * (tm * Pg[ctm] + t0 * b + tp * Pg[ctp]);
+    }
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+        if (ca(q, A) * side < 0) {
+            fb[q] = fb[opp(q)];
+            gb[q] = gb[opp(q)];
+        }
+    }
+    FaceAux<T> ax;
+    ax.mu = P.mu[c];
+    ax.lapmu = P.lapmu[c];
+    ax.gmux = (A == 0) ? T(0) : P.gmux[c];
+    ax.gmuy = (A == 1) ? T(0) : P.gmuy[c];
+    ax.gpx = (A == 0) ? T(0) : P.gpx[c];
+    ax.gpy = (A == 1) ? T(0) : P.gpy[c];
+    ax.gphix = (A == 0) ? T(0) : P.gphix[c];
+    ax.gphiy = (A == 1) ? T(0) : P.gphiy[c];
+    face_originals<T>(I, fb, gb, ax, true, fo, go);
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+        if (ca(q, A) * side < 0) {
+            fo[q] = fo[opp(q)];
+            go[q] = go[opp(q)];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_face: flux through the four faces of each cell (steps 3-5) and the update
+// tilde^{n+1} = 4/3 bar-plus - 1/3 tilde - dt/|V| J (Eqs. relations2, updatef),
+// in place; then phi = sum g for the next step and the non-finite flag.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(TX *TY) k_face(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles,
+                                                 const AxisRec *__restrict__ geo, Planes<T> P)
+{
+    const int4 t = tiles[blockIdx.x];
+    const InstDev &I = insts[t.x];
+    if (P.status[t.x]) return;   // masked: non-finite instance of a batch
+    const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
+    if (i >= I.nx || j >= I.ny) return;
+    const AxisRec &ax = geo[I.gx_off + i];
+    const AxisRec &ay = geo[I.gy_off + j];
+    const long long c = cell_of(I, i, j);
+    const long long N = P.N;
+    T Jf[Q], Jg[Q], fo[Q], go[Q];
+#pragma unroll
+    for (int q = 0; q < Q; q++) { Jf[q] = 0; Jg[q] = 0; }
+    // x faces, area dy
+    const T ay_area = T(ay.d), ax_area = T(ax.d);
+    // west face
+    if (ax.lo_wall) wall_face<T, 0>(I, P, geo, i, j, -1, fo, go);
+    else interior_face<T, 0>(I, P, geo, ax.km, j, i, j, fo, go);
+#pragma unroll
+    for (int q = 0; q < Q; q++) if (cx(q)) { Jf[q] -= T(cx(q)) * fo[q] * ay_area; Jg[q] -= T(cx(q)) * go[q] * ay_area; }
+    // east face
+    if (ax.hi_wall) wall_face<T, 0>(I, P, geo, i, j, +1, fo, go);
+    else interior_face<T, 0>(I, P, geo, i, j, ax.kp, j, fo, go);
+#pragma unroll
+    for (int q = 0; q < Q; q++) if (cx(q)) { Jf[q] += T(cx(q)) * fo[q] * ay_area; Jg[q] += T(cx(q)) * go[q] * ay_area; }
+    // south face
+    if (ay.lo_wall) wall_face<T, 1>(I, P, geo, i, j, -1, fo, go);
+    else interior_face<T, 1>(I, P, geo, i, ay.km, i, j, fo, go);
+#pragma unroll
+    for (int q = 0; q < Q; q++) if (cy(q)) { Jf[q] -= T(cy(q)) * fo[q] * ax_area; Jg[q] -= T(cy(q)) * go[q] * ax_area; }
+    // north face
+    if (ay.hi_wall) wall_face<T, 1>(I, P, geo, i, j, +1, fo, go);
+    else interior_face<T, 1>(I, P, geo, i, j, i, ay.kp, fo, go);
+#pragma unroll
+    for (int q = 0; q < Q; q++) if (cy(q)) { Jf[q] += T(cy(q)) * fo[q] * ax_area; Jg[q] += T(cy(q)) * go[q] * ax_area; }
+
+    const T dtv = T(I.dt) / (ax_area * ay_area);
+    bool finite = true;
+    if constexpr (sizeof(T) == sizeof(double)) {
+        T phi = 0;
+#pragma unroll
+        for (int q = 0; q < Q; q++) {
+            T fn = T(4.0 / 3.0) * P.fbp[q * N + c] - T(1.0 / 3.0) * P.f[q * N + c] - dtv * Jf[q];
+            T gn = T(4.0 / 3.0) * P.gbp[q * N + c] - T(1.0 / 3.0) * P.g[q * N + c] - dtv * Jg[q];
+            P.f[q * N + c] = fn;
+            P.g[q * N + c] = gn;
+            phi += gn;
+            finite = finite && isfinite(fn) && isfinite(gn);
+        }
+        P.phi[c] = phi;
+    } else {
+        // FP32 storage: sum_i g~+_i = phi exactly (Eqs. relations1/2), so the
+        // order parameter advances by the flux balance alone; it is carried in
+        // FP64 and the rest distribution g~_0 is rebuilt from it.
+        T jsum = 0, gsum = 0;
+#pragma unroll
+        for (int q = 0; q < Q; q++) {
+            T fn = T(4.0 / 3.0) * P.fbp[q * N + c] - T(1.0 / 3.0) * P.f[q * N + c] - dtv * Jf[q];
+            P.f[q * N + c] = fn;
+            finite = finite && isfinite(fn);
+            jsum += Jg[q];
+            if (q > 0) {
+                T gn = T(4.0 / 3.0) * P.gbp[q * N + c] - T(1.0 / 3.0) * P.g[q * N + c] - dtv * Jg[q];
+                P.g[q * N + c] = gn;
+                gsum += gn;
+                finite = finite && isfinite(gn);
+            }
+        }
+        const double phi = P.phi[c] - (double)(dtv * jsum);
+        P.phi[c] = phi;
+        P.g[c] = T(phi - (double)gsum);
+        finite = finite && isfinite(phi);
+    }
+    if (!finite) atomicOr(P.status + t.x, 1);
+}
+
+// ---------------------------------------------------------------------------
+// k_init: step 1, tilde = eq - dt/2 F with the given phi, u, p (planes phi,
+// ux, uy, p already hold them; mu was computed by k_mu).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(TX *TY) k_init(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles,
+                                                 const AxisRec *__restrict__ geo, Planes<T> P)
+{
+    const int4 t = tiles[blockIdx.x];
+    const InstDev &I = insts[t.x];
+    const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
+    if (i >= I.nx || j >= I.ny) return;
+    const AxisRec &ax = geo[I.gx_off + i];
+    const AxisRec &ay = geo[I.gy_off + j];
+    const long long c = cell_of(I, i, j);
+    const long long N = P.N;
+    Pt<T> s;
+    s.phi = T(P.phi[c]);
+    s.rho = rho_of<T>(I, s.phi);
+    s.ux = P.ux[c];
+    s.uy = P.uy[c];
+    s.p = P.p[c];
+    s.mu = P.mu[c];
+    T gmx, gmy, gfx, gfy, gpx, gpy;
+    grad_field(I, P.mu, ax, ay, i, j, s.mu, gmx, gmy);
+    grad_phi(I, P.phi, ax, ay, i, j, P.phi[c], gfx, gfy);
+    grad_field(I, P.p, ax, ay, i, j, s.p, gpx, gpy);
+    s.lapmu = (T(ax.c2m) * P.mu[cell_of(I, ax.km, j)] + T(ax.c20) * s.mu + T(ax.c2p) * P.mu[cell_of(I, ax.kp, j)])
+            + (T(ay.c2m) * P.mu[cell_of(I, i, ay.km)] + T(ay.c20) * s.mu + T(ay.c2p) * P.mu[cell_of(I, i, ay.kp)]);
+    s.Fx = -s.phi * gmx + (s.rho - T(I.rho_ref)) * T(I.gxa);
+    s.Fy = -s.phi * gmy + (s.rho - T(I.rho_ref)) * T(I.gya);
+    s.grx = T(I.drho) * gfx;
+    s.gry = T(I.drho) * gfy;
+    s.gpx = gpx;
+    s.gpy = gpy;
+    s.tauf = tauf_of<T>(I, s.phi, s.rho);
+    const T hdt = T(0.5) * T(I.dt);
+    bool finite = true;
+    T gsum = 0;
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+        T feq, geq, Ff, Fg;
+        eq_src<T>(I, s, q, feq, geq, Ff, Fg);
+        T fv = feq - hdt * Ff, gv = geq - hdt * Fg;
+        P.f[q * N + c] = fv;
+        P.g[q * N + c] = gv;
+        if (q > 0) gsum += gv;
+        finite = finite && isfinite(fv) && isfinite(gv);
+    }
+    // FP32 storage: the rest distribution is rebuilt from the FP64 phi (sum g = phi)
+    if constexpr (sizeof(T) != sizeof(double)) P.g[c] = T(P.phi[c] - (double)gsum);
+    if (!finite) atomicOr(P.status + t.x, 1);
+}
+
+// phi = sum g (after init or a state load), in index order 0..8
+template <typename T>
+__global__ void __launch_bounds__(TX *TY) k_phi(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles,
+                                                Planes<T> P)
+{
+    const int4 t = tiles[blockIdx.x];
+    const InstDev &I = insts[t.x];
+    const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
+    if (i >= I.nx || j >= I.ny) return;
+    const long long c = cell_of(I, i, j);
+    double phi = 0;
+#pragma unroll
+    for (int q = 0; q < Q; q++) phi += (double)P.g[q * P.N + c];
+    P.phi[c] = phi;
+}
+
+// ---------------------------------------------------------------------------
+// k_reduce: per-tile FP64 partial sums of |V| phi and |V| rho; a second pass
+// (k_reduce_inst) adds the partials of each instance in tile order.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(TX *TY) k_reduce(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles,
+                                                   const AxisRec *__restrict__ geo, Planes<T> P, double2 *partials)
+{
+    __shared__ double2 red[TX * TY / 32];
+    const int4 t = tiles[blockIdx.x];
+    const InstDev &I = insts[t.x];
+    const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
+    double a = 0.0, b = 0.0;
+    if (i < I.nx && j < I.ny) {
+        const long long c = cell_of(I, i, j);
+        const double phi = P.phi[c];
+        double vol = geo[I.gx_off + i].d * geo[I.gy_off + j].d;
+        a = vol * phi;
+        b = vol * (I.rhoB + I.drho * (phi - I.phiB));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int lane = (threadIdx.y * TX + threadIdx.x) & 31, warp = (threadIdx.y * TX + threadIdx.x) >> 5;
+    if (lane == 0) red[warp] = make_double2(a, b);
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        double2 s = red[0];
+        for (int w = 1; w < TX * TY / 32; w++) { s.x += red[w].x; s.y += red[w].y; }
+        partials[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_reduce_inst(const InstDev *__restrict__ insts, int n_inst, const double2 *__restrict__ partials,
+                              double2 *out)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_inst) return;
+    const InstDev &I = insts[k];
+    double2 s = make_double2(0.0, 0.0);
+    for (int t = 0; t < I.ntiles; t++) {
+        s.x += partials[I.tile0 + t].x;
+        s.y += partials[I.tile0 + t].y;
+    }
+    out[k] = s;
+}
+
+// Gather a padded plane (type T) into a dense double array and back.
+template <typename T>
+__global__ void k_pack(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles, const T *__restrict__ src,
+                       double *__restrict__ dst, const long long *__restrict__ dense0)
+{
+    const int4 t = tiles[blockIdx.x];
+    const InstDev &I = insts[t.x];
+    const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
+    if (i >= I.nx || j >= I.ny) return;
+    dst[dense0[t.x] + (long long)j * I.nx + i] = (double)src[cell_of(I, i, j)];
+}
+
+template <typename T>
+__global__ void k_unpack(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles, const double *__restrict__ src,
+                         T *__restrict__ dst, const long long *__restrict__ dense0)
+{
+    const int4 t = tiles[blockIdx.x];
+    const InstDev &I = insts[t.x];
+    const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
+    if (i >= I.nx || j >= I.ny) return;
+    dst[cell_of(I, i, j)] = (T)src[dense0[t.x] + (long long)j * I.nx + i];
+}
+
+}  // namespace dugks

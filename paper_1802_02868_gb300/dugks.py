@@ -1,0 +1,261 @@
+"""ctypes binding of ``libdugks.so`` (the C ABI of ``include/dugks.h``).
+
+Argument marshalling only: every step of the scheme runs in the library's CUDA
+kernels.  The binding raises if the library is missing or a call fails; there
+is no fallback of any kind.
+
+``Sim`` wraps one simulation or one batch.  Meshes and parameters are the
+``inputs.Mesh`` / ``inputs.Params`` records; fields are numpy float64 arrays
+of shape ``[ny, nx]`` (one instance) or lists of them (a batch).  The CUDA
+stream is the caller's (``torch.cuda.current_stream().cuda_stream`` or 0).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+FP64 = 0
+FP32 = 1
+Q = 9
+
+STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "non-finite state", -4: "out of device memory",
+          -5: "device wait timed out", -6: "unsupported"}
+
+
+class DugksError(RuntimeError):
+    def __init__(self, fn, rc):
+        super().__init__("%s failed: %s (%d)" % (fn, STATUS.get(rc, "?"), rc))
+        self.rc = rc
+
+
+class NonFiniteError(DugksError):
+    pass
+
+
+class Mesh_t(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("dx", ctypes.POINTER(ctypes.c_double)),
+                ("dy", ctypes.POINTER(ctypes.c_double)), ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int)]
+
+
+class Params_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("phiA", "phiB", "rhoA", "rhoB", "nuA", "nuB", "mobility", "tau_g",
+                                               "beta", "kappa", "gx", "gy", "rho_ref", "cfl")] + \
+               [("precision", ctypes.c_int)]
+
+
+_lib = None
+EXPORTS = ("dugks_create", "dugks_batch_create", "dugks_destroy", "dugks_init", "dugks_step", "dugks_moments",
+           "dugks_conservation", "dugks_batch_status", "dugks_dt", "dugks_info", "dugks_save", "dugks_load",
+           "dugks_launch_count", "dugks_set_timing", "dugks_kernel_times", "dugks_kernel_name",
+           "dugks_kernel_bytes_per_cell", "dugks_status_str")
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libdugks.so (building it with nvcc first if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise OSError("libdugks.so is not built: run paper_1802_02868_gb300.build.build()")
+        _build.build()
+    L = ctypes.CDLL(_build.LIB)
+    vp, ip, dp = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double)
+    L.dugks_create.argtypes = [ctypes.POINTER(Mesh_t), ctypes.POINTER(Params_t), vp, ctypes.POINTER(vp)]
+    L.dugks_batch_create.argtypes = [ip, ctypes.POINTER(Mesh_t), ctypes.POINTER(Params_t), vp, ctypes.POINTER(vp)]
+    L.dugks_destroy.argtypes = [vp]
+    L.dugks_destroy.restype = None
+    L.dugks_init.argtypes = [vp, dp, dp, dp, dp]
+    L.dugks_step.argtypes = [vp, ctypes.c_long]
+    L.dugks_moments.argtypes = [vp, dp, dp, dp, dp, dp]
+    L.dugks_conservation.argtypes = [vp, dp, dp]
+    L.dugks_batch_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.dugks_dt.argtypes = [vp, ip, dp]
+    L.dugks_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_long),
+                             ctypes.POINTER(ctypes.c_size_t)]
+    L.dugks_save.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.dugks_load.argtypes = [vp, vp, ctypes.c_size_t]
+    L.dugks_launch_count.argtypes = [vp, ctypes.POINTER(ctypes.c_long)]
+    L.dugks_set_timing.argtypes = [vp, ip]
+    L.dugks_kernel_times.argtypes = [vp, dp, ctypes.POINTER(ctypes.c_long)]
+    L.dugks_kernel_name.argtypes = [ip]
+    L.dugks_kernel_name.restype = ctypes.c_char_p
+    L.dugks_kernel_bytes_per_cell.argtypes = [vp, ip, dp]
+    L.dugks_status_str.argtypes = [ip]
+    L.dugks_status_str.restype = ctypes.c_char_p
+    for n in EXPORTS:
+        if n not in ("dugks_destroy", "dugks_kernel_name", "dugks_status_str"):
+            getattr(L, n).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+NUM_KERNELS = 6
+
+
+def _check(fn, rc):
+    if rc == -3:
+        raise NonFiniteError(fn, rc)
+    if rc != 0:
+        raise DugksError(fn, rc)
+
+
+def _dp(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
+    if a.size != n:
+        raise ValueError("expected %d values, got %d" % (n, a.size))
+    return a
+
+
+class Sim:
+    """One simulation (``meshes`` a single Mesh) or a batch (a list of Mesh)."""
+
+    def __init__(self, meshes, params, precision=FP64, stream=0):
+        L = load()
+        single = not isinstance(meshes, (list, tuple))
+        self.meshes = [meshes] if single else list(meshes)
+        self.params = [params] * len(self.meshes) if not isinstance(params, (list, tuple)) else list(params)
+        if len(self.params) != len(self.meshes):
+            raise ValueError("one Params per mesh")
+        self.single = single
+        n = len(self.meshes)
+        self._keep = []
+        M = (Mesh_t * n)()
+        Pr = (Params_t * n)()
+        for k, (m, p) in enumerate(zip(self.meshes, self.params)):
+            dx = np.ascontiguousarray(m.dx, dtype=np.float64)
+            dy = np.ascontiguousarray(m.dy, dtype=np.float64)
+            self._keep += [dx, dy]
+            M[k] = Mesh_t(int(dx.size), int(dy.size), _dp(dx), _dp(dy), int(m.bc_x), int(m.bc_y))
+            vals = p.as_list()
+            Pr[k] = Params_t(*vals, int(precision))
+        h = ctypes.c_void_p()
+        rc = L.dugks_batch_create(n, M, Pr, ctypes.c_void_p(int(stream)), ctypes.byref(h))
+        _check("dugks_batch_create", rc)
+        self.h = h
+        self.precision = precision
+        self.sizes = [m.nx * m.ny for m in self.meshes]
+        self.ncells = int(sum(self.sizes))
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            load().dugks_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- helpers
+    def _cat(self, fields):
+        if fields is None:
+            return None
+        if self.single or (isinstance(fields, np.ndarray) and fields.size == self.ncells):
+            return _f64(fields, self.ncells)
+        return _f64(np.concatenate([np.asarray(f, dtype=np.float64).reshape(-1) for f in fields]), self.ncells)
+
+    def _split(self, flat):
+        out, o = [], 0
+        for m, n in zip(self.meshes, self.sizes):
+            out.append(flat[o:o + n].reshape(m.ny, m.nx))
+            o += n
+        return out[0] if self.single else out
+
+    # -- ABI calls
+    def init(self, phi, ux=None, uy=None, p=None):
+        arrs = [self._cat(phi), self._cat(ux), self._cat(uy), self._cat(p)]
+        _check("dugks_init", load().dugks_init(self.h, *[_dp(a) for a in arrs]))
+        return self
+
+    def step(self, n=1):
+        _check("dugks_step", load().dugks_step(self.h, int(n)))
+        return self
+
+    def moments(self):
+        out = [np.zeros(self.ncells) for _ in range(5)]
+        _check("dugks_moments", load().dugks_moments(self.h, *[_dp(a) for a in out]))
+        return dict(zip(("phi", "rho", "ux", "uy", "p"), [self._split(a) for a in out]))
+
+    def conservation(self):
+        n = len(self.meshes)
+        a, b = np.zeros(n), np.zeros(n)
+        _check("dugks_conservation", load().dugks_conservation(self.h, _dp(a), _dp(b)))
+        return (a[0], b[0]) if self.single else (a, b)
+
+    def status(self):
+        n = len(self.meshes)
+        st = (ctypes.c_int * n)()
+        _check("dugks_batch_status", load().dugks_batch_status(self.h, st))
+        return list(st)
+
+    def dt(self, k=0):
+        v = ctypes.c_double()
+        _check("dugks_dt", load().dugks_dt(self.h, int(k), ctypes.byref(v)))
+        return v.value
+
+    def state(self):
+        """Tracked tilde state as FP64 arrays (f, g), each [9, cells]."""
+        nb = ctypes.c_size_t(0)
+        _check("dugks_save", load().dugks_save(self.h, None, ctypes.byref(nb)))
+        buf = np.zeros(nb.value // 8)
+        _check("dugks_save", load().dugks_save(self.h, buf.ctypes.data_as(ctypes.c_void_p), ctypes.byref(nb)))
+        buf = buf.reshape(2, Q, self.ncells)
+        if self.single:
+            m = self.meshes[0]
+            return buf[0].reshape(Q, m.ny, m.nx), buf[1].reshape(Q, m.ny, m.nx)
+        return buf[0], buf[1]
+
+    def set_state(self, f, g):
+        buf = np.ascontiguousarray(np.stack([np.asarray(f, dtype=np.float64).reshape(Q, -1),
+                                             np.asarray(g, dtype=np.float64).reshape(Q, -1)]))
+        if buf.shape[2] != self.ncells:
+            raise ValueError("state has %d cells, expected %d" % (buf.shape[2], self.ncells))
+        _check("dugks_load", load().dugks_load(self.h, buf.ctypes.data_as(ctypes.c_void_p), buf.nbytes))
+
+    def launch_count(self):
+        v = ctypes.c_long()
+        _check("dugks_launch_count", load().dugks_launch_count(self.h, ctypes.byref(v)))
+        return v.value
+
+    def set_timing(self, on=True):
+        _check("dugks_set_timing", load().dugks_set_timing(self.h, 1 if on else 0))
+
+    def kernel_times(self):
+        ms = np.zeros(NUM_KERNELS)
+        n = (ctypes.c_long * NUM_KERNELS)()
+        _check("dugks_kernel_times", load().dugks_kernel_times(self.h, _dp(ms), n))
+        return {kernel_name(k): (ms[k], n[k]) for k in range(NUM_KERNELS)}
+
+    def kernel_bytes_per_cell(self, k):
+        v = ctypes.c_double()
+        _check("dugks_kernel_bytes_per_cell", load().dugks_kernel_bytes_per_cell(self.h, int(k), ctypes.byref(v)))
+        return v.value
+
+
+def kernel_name(k):
+    return load().dugks_kernel_name(int(k)).decode()
+
+
+def status_str(rc):
+    return load().dugks_status_str(int(rc)).decode()

@@ -1,0 +1,155 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU FP64 oracle on
+the same seeded inputs.  FP64: normwise relative error of each distribution set
+<= 1e-12 per step (one step from an identical state) and <= 1e-10 after 50
+steps; FP32: phi L-inf <= 1e-5 and u L2-relative <= 1e-4 after the run."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1802_02868_gb300 import dugks
+from paper_1802_02868_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def normwise(a, b):
+    d = np.max(np.abs(np.asarray(a) - np.asarray(b)))
+    s = np.max(np.abs(b))
+    return d / max(s, 1e-300)
+
+
+def _cases():
+    rng = np.random.default_rng(7)
+    out = []
+    c = I.stationary_drop(n=64, radius=16.0)
+    out.append(("drop64", c))
+    c = I.layered_poiseuille(nx=4, ny=64, height=64.0, nu_ratio=10.0, force=1e-5)
+    out.append(("poiseuille_4x64_walls", c))
+    c = I.rayleigh_taylor(nx=32, ny=96, amplitudes=[3.2])
+    out.append(("rt_32x96", c))
+    # ragged sizes, non-uniform spacing in both axes, walls in x and y
+    m = I.Mesh(1.0 + 0.5 * rng.random(37), 0.7 + 0.6 * rng.random(29), I.WALL, I.WALL)
+    beta, kappa = I.params_from_sigma_width(2e-3, 4.0)
+    p = I.Params(rhoA=3.0, rhoB=1.0, nuA=0.2, nuB=0.05, mobility=0.2, tau_g=0.7, beta=beta, kappa=kappa,
+                 gx=2e-6, gy=-1e-5, rho_ref=2.0, cfl=0.7)
+    phi = I.drop_field(m, 8.0, (20.0, 12.0), 4.0)
+    out.append(("ragged_37x29_walls", I.Case("ragged", m, p, phi)))
+    # degenerate sizes
+    for nx, ny, bcx, bcy in ((1, 16, I.PERIODIC, I.PERIODIC), (3, 3, I.PERIODIC, I.PERIODIC),
+                             (2, 5, I.PERIODIC, I.WALL), (33, 9, I.WALL, I.PERIODIC)):
+        m = I.Mesh(1.0 + 0.2 * rng.random(nx), 1.0 + 0.2 * rng.random(ny), bcx, bcy)
+        phi = 0.5 + 0.4 * np.sin(np.arange(nx * ny).reshape(ny, nx) * 0.7)
+        out.append(("tiny_%dx%d" % (nx, ny), I.Case("tiny", m, I.Params(rhoA=2.0, rhoB=1.0, beta=beta, kappa=kappa,
+                                                                          gy=-1e-5, rho_ref=1.5), phi)))
+    return out
+
+
+CASES = _cases()
+
+
+@pytest.mark.parametrize("name,case", CASES, ids=[c[0] for c in CASES])
+def test_fp64_init_and_single_step_parity(name, case):
+    o = oracle.Oracle(case.mesh, case.params).init(case.phi0)
+    s = dugks.Sim(case.mesh, case.params, dugks.FP64).init(case.phi0)
+    assert s.dt() == pytest.approx(o.dt, rel=1e-15)
+    fo, go = o.state()
+    fs, gs = s.state()
+    # at t = 0 the f distributions are O(dt |F|), set by mu's cancellation of
+    # psi' against kappa lap(phi): a looser bound than for a developed state
+    assert normwise(fs, fo) < 1e-12 and normwise(gs, go) < 1e-13
+    # advance the oracle, load its state into the GPU, and compare one step
+    o.step(200)
+    fo, go = o.state()
+    s.set_state(fo, go)
+    o.step(1)
+    s.step(1)
+    fo1, go1 = o.state()
+    fs1, gs1 = s.state()
+    ef, eg = normwise(fs1, fo1), normwise(gs1, go1)
+    assert ef < 1e-12 and eg < 1e-12, (ef, eg)
+
+
+@pytest.mark.parametrize("name,case", CASES[:4], ids=[c[0] for c in CASES[:4]])
+def test_fp64_multi_step_parity_and_moments(name, case):
+    o = oracle.Oracle(case.mesh, case.params).init(case.phi0)
+    s = dugks.Sim(case.mesh, case.params, dugks.FP64).init(case.phi0)
+    o.step(50)
+    s.step(50)
+    fo, go = o.state()
+    fs, gs = s.state()
+    assert normwise(fs, fo) < 1e-10 and normwise(gs, go) < 1e-10
+    mo, ms = o.moments(), s.moments()
+    for k in ("phi", "rho", "p"):
+        assert normwise(ms[k], mo[k]) < 1e-10, k
+    u_scale = max(np.abs(mo["ux"]).max(), np.abs(mo["uy"]).max())
+    assert np.abs(ms["ux"] - mo["ux"]).max() < 1e-9 * u_scale
+    assert np.abs(ms["uy"] - mo["uy"]).max() < 1e-9 * u_scale
+    so, ss = o.conservation(), s.conservation()
+    assert ss[0] == pytest.approx(so[0], rel=1e-12)
+
+
+def test_fp64_conservation_on_gpu():
+    c = I.rayleigh_taylor(nx=64, ny=128, amplitudes=[6.4])
+    s = dugks.Sim(c.mesh, c.params, dugks.FP64).init(c.phi0)
+    a0 = s.conservation()[0]
+    s.step(500)
+    a1 = s.conservation()[0]
+    assert abs(a1 - a0) < 1e-12 * abs(a0)
+
+
+def test_fp32_drop_accuracy_against_fp64_oracle():
+    """Stationary drop 64x64, rho ratio 10, 2000 steps: FP32 storage and arithmetic."""
+    c = I.stationary_drop()
+    o = oracle.Oracle(c.mesh, c.params).init(c.phi0)
+    s = dugks.Sim(c.mesh, c.params, dugks.FP32).init(c.phi0)
+    o.step(c.steps)
+    s.step(c.steps)
+    mo, ms = o.moments(), s.moments()
+    assert np.abs(ms["phi"] - mo["phi"]).max() <= 1e-5
+    uo = np.hypot(mo["ux"], mo["uy"])
+    du = np.hypot(ms["ux"] - mo["ux"], ms["uy"] - mo["uy"])
+    assert np.linalg.norm(du) / np.linalg.norm(uo) <= 1e-4
+
+
+def test_batch_matches_oracle_per_instance():
+    """Uneven instances (different sizes, BCs and parameters) in one batch."""
+    cases = [c for _, c in CASES[:4]] + I.batched_ensemble(3, seed=5, sides=(48, 64))
+    s = dugks.Sim([c.mesh for c in cases], [c.params for c in cases], dugks.FP64)
+    s.init([c.phi0 for c in cases])
+    s.step(20)
+    fs, gs = s.state()
+    off = 0
+    for c in cases:
+        o = oracle.Oracle(c.mesh, c.params).init(c.phi0)
+        o.step(20)
+        fo, go = o.state()
+        n = c.mesh.ncells
+        assert normwise(fs[:, off:off + n], fo.reshape(9, -1)) < 1e-11
+        assert normwise(gs[:, off:off + n], go.reshape(9, -1)) < 1e-11
+        off += n
+    assert s.status() == [0] * len(cases)
+
+
+def test_nonfinite_state_is_reported():
+    """A host-made state whose arithmetic overflows raises the non-finite status."""
+    c = I.stationary_drop(n=32, radius=8.0)
+    s = dugks.Sim(c.mesh, c.params, dugks.FP64).init(c.phi0)
+    f, g = s.state()
+    f = f.copy()
+    f[:, 10, 10] = 1e306
+    s.set_state(f, g)
+    s.step(3)
+    with pytest.raises(dugks.NonFiniteError):
+        s.moments()
+    assert s.status() == [-3]
+
+
+def test_invalid_init_input_rejected():
+    c = I.stationary_drop(n=16, radius=4.0)
+    s = dugks.Sim(c.mesh, c.params, dugks.FP64)
+    phi = c.phi0.copy()
+    phi[3, 3] = math.nan
+    with pytest.raises(dugks.NonFiniteError):
+        s.init(phi)
