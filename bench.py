@@ -49,8 +49,9 @@ def workload(name, seed):
         cases = [I.stationary_drop()]
         desc = {"workload": "stationary drop 64x64 periodic, rho ratio 10", "instances": 1}
     elif name == "roofline":
-        cases = [I.roofline_drop()]
-        desc = {"workload": "roofline drop 4096x4096 periodic, R=1024", "instances": 1}
+        n = int(os.environ.get("DUGKS_ROOFLINE_N", "4096"))
+        cases = [I.roofline_drop(n)]
+        desc = {"workload": "roofline drop %dx%d periodic, R=%d" % (n, n, n // 4), "instances": 1}
     else:
         raise SystemExit("unknown workload %s" % name)
     desc["cells"] = int(sum(c.mesh.ncells for c in cases))

@@ -130,7 +130,7 @@ int dugks_launch_count(const dugks_sim *sim, long *count);
    accumulated milliseconds and launch counts per kernel with
    dugks_kernel_times (arrays of DUGKS_NUM_KERNELS entries, names by
    dugks_kernel_name).  Synchronises on read. */
-#define DUGKS_NUM_KERNELS 6
+#define DUGKS_NUM_KERNELS 7
 int dugks_set_timing(dugks_sim *sim, int enable);
 int dugks_kernel_times(dugks_sim *sim, double *ms, long *launches);
 const char *dugks_kernel_name(int k);

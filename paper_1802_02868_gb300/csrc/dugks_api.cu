@@ -6,13 +6,16 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/dugks.h"
 #include "dugks_common.cuh"
 #include "dugks_kernels.cuh"
+#include "dugks_fused.cuh"
 
 using namespace dugks;
 
@@ -38,9 +41,15 @@ struct dugks_sim {
     InstDev *d_inst = nullptr;
     int4 *d_tiles = nullptr;
     AxisRec *d_geo = nullptr;
+    void *d_geoT = nullptr;       // the same records in the arithmetic type of the sim
     long long *d_dense0 = nullptr;
     void *d_planes = nullptr;     // one allocation for all planes of type T
     double *d_phi = nullptr;      // FP64 order parameter plane
+    void *d_alt_alloc = nullptr;  // second state buffer (f, g) for the fused step
+    double *d_phi_alt_alloc = nullptr;
+    void *d_alt = nullptr;        // the state buffer not holding the current state
+    double *d_phi_alt = nullptr;
+    bool fused = true;            // one-launch step (k_step) or the four-kernel step
     int *d_status = nullptr;
     double2 *d_partials = nullptr;
     double2 *d_sums = nullptr;
@@ -57,7 +66,7 @@ struct dugks_sim {
 
 namespace {
 
-const char *kNames[K_COUNT] = {"k_mu", "k_macro", "k_cell", "k_face", "k_init", "k_reduce"};
+const char *kNames[K_COUNT] = {"k_mu", "k_macro", "k_cell", "k_face", "k_init", "k_reduce", "k_step"};
 
 int cuda_status(cudaError_t e)
 {
@@ -191,8 +200,36 @@ void harvest_events(dugks_sim *s)
 }
 
 template <typename T>
+int launch_fused(dugks_sim *s)
+{
+    using L = FusedLayout<T, TX, TY>;
+    constexpr int MINB = sizeof(T) == 4 ? 2 : 1;   // resident CTAs per SM the registers are sized for
+    static bool attr_set = false;   // per instantiation; set before the first launch
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_step<T, TX, TY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+        if (e != cudaSuccess) return cuda_status(e);
+        attr_set = true;
+    }
+    Planes<T> &P = planes<T>(s);
+    // the other state buffer: f then g, Q planes each, and its phi plane
+    T *alt = (T *)s->d_alt;
+    StepIO<T> io;
+    io.f_in = P.f; io.g_in = P.g; io.phi_in = P.phi;
+    io.f_out = alt; io.g_out = alt + (long long)Q * P.N; io.phi_out = (phi_t<T> *)s->d_phi_alt;
+    io.N = P.N;
+    io.status = s->d_status;
+    { Timed t(s, K_STEP); k_step<T, TX, TY, MINB><<<(unsigned)s->n_tiles, dim3(TX, TY), L::bytes, s->stream>>>(s->d_inst, s->d_tiles, (const AxisRecT<T> *)s->d_geoT, io); }
+    // swap: the new state becomes current for every other kernel
+    s->d_alt = (void *)P.f;
+    s->d_phi_alt = (double *)P.phi;
+    P.f = io.f_out; P.g = io.g_out; P.phi = io.phi_out;
+    return cuda_status(cudaGetLastError());
+}
+
+template <typename T>
 int launch_step(dugks_sim *s)
 {
+    if (s->fused) return launch_fused<T>(s);
     Planes<T> &P = planes<T>(s);
     const dim3 blk(TX, TY);
     const unsigned g = (unsigned)s->n_tiles;
@@ -210,7 +247,7 @@ int do_init(dugks_sim *s)
     const dim3 blk(TX, TY);
     const unsigned g = (unsigned)s->n_tiles;
     const long long D = s->n_dense;
-    { Timed t(s, -1); k_unpack<double><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_stage + 0 * D, P.phi, s->d_dense0); }
+    { Timed t(s, -1); k_unpack_phi<phi_t<T>><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_stage + 0 * D, P.phi, s->d_dense0); }
     { Timed t(s, -1); k_unpack<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_stage + 1 * D, P.ux, s->d_dense0); }
     { Timed t(s, -1); k_unpack<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_stage + 2 * D, P.uy, s->d_dense0); }
     { Timed t(s, -1); k_unpack<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_stage + 3 * D, P.p, s->d_dense0); }
@@ -231,7 +268,7 @@ int do_moments(dugks_sim *s)
     const long long D = s->n_dense;
     { Timed t(s, K_MU); k_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P); }
     { Timed t(s, K_MACRO); k_macro<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, 1); }
-    { Timed t(s, -1); k_pack<double><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, P.phi, s->d_stage, s->d_dense0); }
+    { Timed t(s, -1); k_pack_phi<phi_t<T>><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, P.phi, s->d_stage, s->d_dense0); }
     T *src[4] = {P.rho, P.ux, P.uy, P.p};
     for (int k = 0; k < 4; k++) {
         Timed t(s, -1);
@@ -286,11 +323,15 @@ void assign_planes(dugks_sim *s, Planes<T> &P, T *base)
     T *p = base;
     P.f = p; p += Q * N;
     P.g = p; p += Q * N;
-    P.fbp = p; p += Q * N;
-    P.gbp = p; p += Q * N;
+    if (s->fused) {
+        P.fbp = P.gbp = nullptr;
+    } else {
+        P.fbp = p; p += Q * N;
+        P.gbp = p; p += Q * N;
+    }
     T **one[] = {&P.mu, &P.lapmu, &P.gmux, &P.gmuy, &P.gphix, &P.gphiy, &P.p, &P.ux, &P.uy, &P.gpx, &P.gpy, &P.rho};
     for (T **q : one) { *q = p; p += N; }
-    P.phi = s->d_phi;
+    P.phi = (phi_t<T> *)s->d_phi;
     P.N = N;
     P.status = s->d_status;
 }
@@ -303,9 +344,12 @@ void free_sim(dugks_sim *s)
     cudaFree(s->d_inst);
     cudaFree(s->d_tiles);
     cudaFree(s->d_geo);
+    cudaFree(s->d_geoT);
     cudaFree(s->d_dense0);
     cudaFree(s->d_planes);
     cudaFree(s->d_phi);
+    cudaFree(s->d_alt_alloc);
+    cudaFree(s->d_phi_alt_alloc);
     cudaFree(s->d_status);
     cudaFree(s->d_partials);
     cudaFree(s->d_sums);
@@ -348,6 +392,10 @@ int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *para
     if (!s) return DUGKS_ERR_OOM;
     s->n_inst = n;
     s->prec = params[0].precision;
+    {
+        const char *env = std::getenv("DUGKS_UNFUSED");
+        s->fused = !(env && env[0] == '1');
+    }
     s->stream = (cudaStream_t)cuda_stream;
     std::vector<AxisRec> geo;
     std::vector<int4> tiles;
@@ -384,6 +432,19 @@ int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *para
         const double rr = p.rhoA / p.rhoB;
         I.gamma = (rr - 1.0) / (p.phiA - p.phiB * rr);  // Eq. (Gama)
         I.drho = (p.rhoA - p.rhoB) / (p.phiA - p.phiB); // Eq. (oderrho)
+        auto split = [](double v) { PhiC c; c.d = v; c.hi = (float)v; c.lo = (float)(v - (double)c.hi); return c; };
+        I.cA = split(p.phiA);
+        I.cB = split(p.phiB);
+        I.cM = split(0.5 * (p.phiA + p.phiB));
+        auto fill = [&](auto &P) {
+            using U = std::remove_reference_t<decltype(P.phiA)>;
+            P.phiA = (U)I.phiA; P.phiB = (U)I.phiB; P.rhoA = (U)I.rhoA; P.rhoB = (U)I.rhoB;
+            P.muA = (U)I.muA; P.muB = (U)I.muB; P.lambda = (U)I.lambda; P.tau_g = (U)I.tau_g;
+            P.beta = (U)I.beta; P.kappa = (U)I.kappa; P.gxa = (U)I.gxa; P.gya = (U)I.gya; P.rho_ref = (U)I.rho_ref;
+            P.dt = (U)I.dt; P.h = (U)I.h; P.eta = (U)I.eta; P.gamma = (U)I.gamma; P.drho = (U)I.drho;
+        };
+        fill(I.pd);
+        fill(I.pf);
         I.tile0 = (int)tiles.size();
         for (int ty = 0; ty < m.ny; ty += TY)
             for (int tx = 0; tx < m.nx; tx += TX) tiles.push_back(make_int4(k, tx, ty, 0));
@@ -394,15 +455,35 @@ int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *para
     s->n_dense = dense;
     s->n_tiles = (int)tiles.size();
     const size_t esz = s->prec == DUGKS_FP64 ? sizeof(double) : sizeof(float);
-    const size_t plane_elems = (size_t)(4 * Q + kNumScalarPlanes) * (size_t)s->N;
+    // the bar-plus planes exist only for the four-kernel step
+    const size_t plane_elems = (size_t)((s->fused ? 2 : 4) * Q + kNumScalarPlanes) * (size_t)s->N;
     cudaError_t e = cudaSuccess;
     auto chk = [&](cudaError_t r) { if (r != cudaSuccess && e == cudaSuccess) e = r; };
     chk(cudaMalloc(&s->d_inst, sizeof(InstDev) * n));
     chk(cudaMalloc(&s->d_tiles, sizeof(int4) * tiles.size()));
     chk(cudaMalloc(&s->d_geo, sizeof(AxisRec) * geo.size()));
+    // typed copy of the geometry for the fused step
+    std::vector<AxisRecT<double>> g64;
+    std::vector<AxisRecT<float>> g32;
+    for (const AxisRec &r : geo) {
+        AxisRecT<double> a{r.d, r.c1m, r.c10, r.c1p, r.c2m, r.c20, r.c2p, r.e1m, r.e10, r.e1p, r.wL, r.wR, r.invd,
+                           r.km, r.kp, r.lo_wall, r.hi_wall};
+        AxisRecT<float> b{(float)r.d, (float)r.c1m, (float)r.c10, (float)r.c1p, (float)r.c2m, (float)r.c20,
+                          (float)r.c2p, (float)r.e1m, (float)r.e10, (float)r.e1p, (float)r.wL, (float)r.wR,
+                          (float)r.invd, r.km, r.kp, r.lo_wall, r.hi_wall};
+        g64.push_back(a);
+        g32.push_back(b);
+    }
+    const bool is64 = s->prec == DUGKS_FP64;
+    const size_t geoT_bytes = is64 ? sizeof(AxisRecT<double>) * g64.size() : sizeof(AxisRecT<float>) * g32.size();
+    chk(cudaMalloc(&s->d_geoT, geoT_bytes));
     chk(cudaMalloc(&s->d_dense0, sizeof(long long) * n));
     chk(cudaMalloc(&s->d_planes, esz * plane_elems));
     chk(cudaMalloc(&s->d_phi, sizeof(double) * (size_t)s->N));
+    chk(cudaMalloc(&s->d_alt_alloc, esz * 2 * Q * (size_t)s->N));
+    chk(cudaMalloc(&s->d_phi_alt_alloc, sizeof(double) * (size_t)s->N));
+    s->d_alt = s->d_alt_alloc;
+    s->d_phi_alt = s->d_phi_alt_alloc;
     chk(cudaMalloc(&s->d_status, sizeof(int) * n));
     chk(cudaMalloc(&s->d_partials, sizeof(double2) * tiles.size()));
     chk(cudaMalloc(&s->d_sums, sizeof(double2) * n));
@@ -415,9 +496,12 @@ int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *para
     chk(cudaMemcpy(s->d_inst, s->h_inst.data(), sizeof(InstDev) * n, cudaMemcpyHostToDevice));
     chk(cudaMemcpy(s->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice));
     chk(cudaMemcpy(s->d_geo, geo.data(), sizeof(AxisRec) * geo.size(), cudaMemcpyHostToDevice));
+    chk(cudaMemcpy(s->d_geoT, is64 ? (const void *)g64.data() : (const void *)g32.data(), geoT_bytes, cudaMemcpyHostToDevice));
     chk(cudaMemcpy(s->d_dense0, s->h_dense0.data(), sizeof(long long) * n, cudaMemcpyHostToDevice));
     chk(cudaMemset(s->d_planes, 0, esz * plane_elems));
     chk(cudaMemset(s->d_phi, 0, sizeof(double) * (size_t)s->N));
+    chk(cudaMemset(s->d_alt_alloc, 0, esz * 2 * Q * (size_t)s->N));
+    chk(cudaMemset(s->d_phi_alt_alloc, 0, sizeof(double) * (size_t)s->N));
     chk(cudaMemset(s->d_status, 0, sizeof(int) * n));
     if (e != cudaSuccess) {
         int rc = cuda_status(e);
@@ -610,6 +694,7 @@ int dugks_kernel_bytes_per_cell(const dugks_sim *s, int k, double *bytes)
     case K_FACE: b = (18 + 8 + 18 + 18) * w + (f64 ? 8 : 16); break; // bar-plus, aux, tilde r/w, phi
     case K_INIT: b = 8 + 4 * w + 18 * w; break;
     case K_REDUCE: b = 8; break;
+    case K_STEP: b = 2 * (2 * Q) * w + 16; break;                   // tilde f, g and phi, read once and written once
     }
     *bytes = b;
     return DUGKS_OK;

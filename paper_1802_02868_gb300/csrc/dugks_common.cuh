@@ -39,6 +39,73 @@ struct AxisRec {
 };
 static_assert(sizeof(AxisRec) == 128, "AxisRec layout");
 
+// Storage of the order parameter phi.  FP64 mode: a double.  FP32 mode: an
+// unevaluated pair of floats (hi + lo, |lo| <= ulp(hi)/2), so that the
+// differences that feed lap(phi) and grad(phi), and the conservative update of
+// phi, keep about 48 bits without a single FP64 instruction in the kernels.
+template <typename T>
+struct PhiS;
+template <>
+struct PhiS<double> { using type = double; };
+template <>
+struct PhiS<float> { using type = float2; };
+template <typename T>
+using phi_t = typename PhiS<T>::type;
+
+__device__ __forceinline__ double phi_val(double v) { return v; }
+__device__ __forceinline__ float phi_val(float2 v) { return v.x + v.y; }
+// a - b
+__device__ __forceinline__ double phi_sub(double a, double b) { return a - b; }
+__device__ __forceinline__ float phi_sub(float2 a, float2 b) { return (a.x - b.x) + (a.y - b.y); }
+// a + d: exact two-sum of the high parts, error folded into the low part
+__device__ __forceinline__ double phi_add(double a, double d) { return a + d; }
+__device__ __forceinline__ float2 phi_add(float2 a, float d)
+{
+    const float s = a.x + d;
+    const float bb = s - a.x;
+    const float e = (a.x - (s - bb)) + (d - bb);
+    const float lo = a.y + e;
+    const float hi = s + lo;
+    return make_float2(hi, lo - (hi - s));
+}
+__device__ __forceinline__ void phi_from_zero(double &v) { v = 0.0; }
+__device__ __forceinline__ void phi_from_zero(float2 &v) { v = make_float2(0.f, 0.f); }
+__device__ __forceinline__ double phi_to_double(double v) { return v; }
+__device__ __forceinline__ double phi_to_double(float2 v) { return (double)v.x + (double)v.y; }
+__device__ __forceinline__ void phi_from_double(double d, double &out) { out = d; }
+__device__ __forceinline__ void phi_from_double(double d, float2 &out)
+{
+    const float hi = (float)d;
+    out = make_float2(hi, (float)(d - (double)hi));
+}
+
+// Model parameters of one instance in the arithmetic type T (precomputed on
+// the host so that FP32 kernels execute no conversion from FP64).
+template <typename T>
+struct ParT {
+    T phiA, phiB, rhoA, rhoB, muA, muB, lambda, tau_g, beta, kappa, gxa, gya, rho_ref;
+    T dt, h, eta, gamma, drho;
+};
+
+// A constant of the phi storage: the double and its float pair (hi, lo).
+struct PhiC {
+    double d;
+    float hi, lo;
+};
+__device__ __forceinline__ double phi_subc(double a, const PhiC &c) { return a - c.d; }
+__device__ __forceinline__ float phi_subc(float2 a, const PhiC &c) { return (a.x - c.hi) + (a.y - c.lo); }
+// a - t for a value t of the arithmetic type
+__device__ __forceinline__ double phi_subt(double a, double t) { return a - t; }
+__device__ __forceinline__ float phi_subt(float2 a, float t) { return (a.x - t) + a.y; }
+
+// Geometry record of one axis position in the arithmetic type T (same fields
+// as AxisRec).
+template <typename T>
+struct AxisRecT {
+    T d, c1m, c10, c1p, c2m, c20, c2p, e1m, e10, e1p, wL, wR, invd;
+    int km, kp, lo_wall, hi_wall;
+};
+
 // Per-instance constants.
 struct InstDev {
     int nx, ny, nxp, bcx, bcy, pad0;
@@ -51,7 +118,18 @@ struct InstDev {
     // derived: dt (Eq. cfl), h = dt/2, eta (Eq. kineticandmobility), gamma (Eq. Gama),
     // drho = d rho / d phi (Eq. oderrho)
     double dt, h, eta, gamma, drho;
+    // phiA, phiB and (phiA + phiB)/2 as constants of the phi storage
+    PhiC cA, cB, cM;
+    ParT<double> pd;
+    ParT<float> pf;
 };
+
+template <typename T>
+__device__ __forceinline__ const ParT<T> &par(const InstDev &I);
+template <>
+__device__ __forceinline__ const ParT<double> &par<double>(const InstDev &I) { return I.pd; }
+template <>
+__device__ __forceinline__ const ParT<float> &par<float>(const InstDev &I) { return I.pf; }
 
 // All device planes of a simulation.  Distribution planes are [Q][N], the
 // rest [N], N = total padded cells of all instances.
@@ -61,7 +139,7 @@ struct Planes {
     T *fbp, *gbp;  // bar-plus at cell centres (step 2)
     // phi is FP64 in both precisions: in FP32 mode it is the authoritative
     // order parameter, advanced by the conservative flux form of the update
-    double *phi;
+    phi_t<T> *phi;
     T *mu, *lapmu, *gmux, *gmuy, *gphix, *gphiy, *p, *ux, *uy, *gpx, *gpy, *rho;
     long long N;
     int *status;   // per instance, bit 0 = non-finite seen
@@ -70,6 +148,6 @@ struct Planes {
 constexpr int TX = 32;
 constexpr int TY = 8;
 
-enum KernelId { K_MU = 0, K_MACRO = 1, K_CELL = 2, K_FACE = 3, K_INIT = 4, K_REDUCE = 5, K_COUNT = 6 };
+enum KernelId { K_MU = 0, K_MACRO = 1, K_CELL = 2, K_FACE = 3, K_INIT = 4, K_REDUCE = 5, K_STEP = 6, K_COUNT = 7 };
 
 }  // namespace dugks

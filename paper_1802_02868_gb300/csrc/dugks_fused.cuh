@@ -1,0 +1,586 @@
+// dugks_fused.cuh -- the whole DUGKS step (Sec. 2.2, steps 2-7) as one tiled
+// kernel for sm_103a.
+//
+// A CTA owns a BX x BY tile of one instance and keeps everything it needs in
+// shared memory, so the step reads the tracked state once and writes it once:
+//   phase 1  phi on the tile plus a 4-cell ring                   (R4)
+//   phase 2  mu = psi'(phi) - kappa lap(phi)                      (R3, Eq. chemicalpotential)
+//   phase 3  p from f~ and F = -phi grad mu + F_b                 (R2, Eqs. u, P)
+//   phase 4  grad p, tau_f, equilibria, sources, bar-plus         (R1, Eq. relations1)
+//   phase 5  all faces of the tile, each once: reconstruction at t+h, face
+//            macros, originals, flux                              (Eqs. fbar_h, conservedVariable
+//                                                                  with h, original-function, microfluxf)
+//   phase 6  tilde^{n+1} = 4/3 bar-plus - 1/3 tilde - dt/|V| J    (Eqs. relations2, updatef)
+// Only the six flux-carrying directions of a face get equilibria, sources and
+// originals.  The ring cells are recomputed by the neighbouring tiles instead
+// of being written to and re-read from HBM; the state is double-buffered
+// because tiles read the old state of their ring.
+#pragma once
+#include "dugks_kernels.cuh"
+
+namespace dugks {
+
+template <typename T>
+struct StepIO {
+    const T *f_in, *g_in;
+    const phi_t<T> *phi_in;
+    T *f_out, *g_out;
+    phi_t<T> *phi_out;
+    long long N;
+    int *status;
+};
+
+template <typename T, int BX, int BY>
+struct FusedLayout {
+    static constexpr int W1 = BX + 2, H1 = BY + 2, A1 = W1 * H1;
+    static constexpr int W2 = BX + 4, H2 = BY + 4, A2 = W2 * H2;
+    static constexpr int W3 = BX + 6, H3 = BY + 6, A3 = W3 * H3;
+    static constexpr int W4 = BX + 8, H4 = BY + 8, A4 = W4 * H4;
+    static constexpr int NG = W4 + H4;                       // geometry entries (x then y)
+    static constexpr int NFX = (BX + 1) * BY, NFY = BX * (BY + 1), NFT = NFX + NFY;
+    static constexpr int NR1 = 7 + 18;                       // R1 planes
+    static constexpr size_t al(size_t v) { return (v + 15) / 16 * 16; }
+    static constexpr size_t o_geo = 0;                       // 11 T arrays + 2 int arrays of NG
+    static constexpr size_t o_un = al(o_geo + (sizeof(T) * 11 + sizeof(int) * 2) * NG);
+    static constexpr size_t un_phi = sizeof(phi_t<T>) * A4;
+    static constexpr size_t un_flux = sizeof(T) * 12 * NFT;
+    static constexpr size_t o_mu = al(o_un + (un_phi > un_flux ? un_phi : un_flux));
+    static constexpr size_t o_p = al(o_mu + sizeof(T) * A3);
+    static constexpr size_t o_r1 = al(o_p + sizeof(T) * A2);
+    static constexpr size_t o_f = al(o_r1 + sizeof(T) * NR1 * A1);   // tilde f on R2, [Q][A2]
+    static constexpr size_t o_g = al(o_f + sizeof(T) * Q * A2);      // tilde g on R1, [Q][A1]
+    static constexpr size_t bytes = al(o_g + sizeof(T) * Q * A1);
+};
+
+// Asynchronous global -> shared copies (cp.async), grouped and awaited.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *dst_smem, const void *src_gmem)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src_gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Flux-carrying directions of x faces (cx != 0) and of y faces (cy != 0).
+__host__ __device__ constexpr int xset(int k) { return k == 0 ? 1 : k == 1 ? 3 : k + 3; }   // 1,3,5,6,7,8
+__host__ __device__ constexpr int yset(int k) { return k == 0 ? 2 : k == 1 ? 4 : k + 3; }   // 2,4,5,6,7,8
+template <int A>
+__host__ __device__ constexpr int fset(int k) { return A == 0 ? xset(k) : yset(k); }
+
+// Geometry of one region position on one axis, read from the SoA arrays.
+template <typename T>
+struct G1 {
+    T c1m, c1p, c2m, c2p, e1m, e10, e1p, wL, wR, invd, d;
+    int g, om, op, lo, hi;
+};
+
+// Shared-memory views of one CTA.
+template <typename T, int BX, int BY>
+struct Tile {
+    using L = FusedLayout<T, BX, BY>;
+    T *ga;          // [11][NG] geometry coefficients, positions x -4..BX+3 then y -4..BY+3
+    int *gg, *gf;   // [NG] global index (-1 outside), flags: 1 om=-1, 2 op=+1, 4 lo wall, 8 hi wall
+    phi_t<T> *phi;  // R4
+    T *flux;        // [12][NFT], aliases phi (phi is dead once phase 4 ends)
+    T *mu;          // R3
+    T *p;           // R2
+    T *gmx, *gmy, *lmu, *gfx, *gfy, *gpx, *gpy;  // R1
+    T *bp;          // [18][A1]: f bar-plus (0..8), g bar-plus (9..17)
+    T *sf;          // tilde f on R2 [Q][A2]
+    T *sg;          // tilde g on R1 [Q][A1]
+    __device__ Tile(unsigned char *sm)
+    {
+        ga = (T *)(sm + L::o_geo);
+        gg = (int *)(ga + 11 * L::NG);
+        gf = gg + L::NG;
+        phi = (phi_t<T> *)(sm + L::o_un);
+        flux = (T *)(sm + L::o_un);
+        mu = (T *)(sm + L::o_mu);
+        p = (T *)(sm + L::o_p);
+        T *r1 = (T *)(sm + L::o_r1);
+        gmx = r1; gmy = r1 + L::A1; lmu = r1 + 2 * L::A1; gfx = r1 + 3 * L::A1; gfy = r1 + 4 * L::A1;
+        gpx = r1 + 5 * L::A1; gpy = r1 + 6 * L::A1;
+        bp = r1 + 7 * L::A1;
+        sf = (T *)(sm + L::o_f);
+        sg = (T *)(sm + L::o_g);
+    }
+    static __device__ __forceinline__ int i1(int x, int y) { return (y + 1) * L::W1 + (x + 1); }
+    static __device__ __forceinline__ int i2(int x, int y) { return (y + 2) * L::W2 + (x + 2); }
+    static __device__ __forceinline__ int i3(int x, int y) { return (y + 3) * L::W3 + (x + 3); }
+    static __device__ __forceinline__ int i4(int x, int y) { return (y + 4) * L::W4 + (x + 4); }
+    // entry of x position x (axis 0) or y position y (axis 1)
+    static __device__ __forceinline__ int ge(int axis, int pos) { return axis == 0 ? pos + 4 : L::W4 + pos + 4; }
+    __device__ __forceinline__ int gidx(int axis, int pos) const { return gg[ge(axis, pos)]; }
+    __device__ __forceinline__ G1<T> geo(int axis, int pos) const
+    {
+        const int e = ge(axis, pos);
+        G1<T> G;
+        G.c1m = ga[0 * L::NG + e]; G.c1p = ga[1 * L::NG + e]; G.c2m = ga[2 * L::NG + e]; G.c2p = ga[3 * L::NG + e];
+        G.e1m = ga[4 * L::NG + e]; G.e10 = ga[5 * L::NG + e]; G.e1p = ga[6 * L::NG + e];
+        G.wL = ga[7 * L::NG + e]; G.wR = ga[8 * L::NG + e]; G.invd = ga[9 * L::NG + e]; G.d = ga[10 * L::NG + e];
+        const int f = gf[e];
+        G.g = gg[e];
+        G.om = (f & 1) ? -1 : 0;
+        G.op = (f & 2) ? 1 : 0;
+        G.lo = (f >> 2) & 1;
+        G.hi = (f >> 3) & 1;
+        return G;
+    }
+    __device__ __forceinline__ int om(int axis, int pos) const { return (gf[ge(axis, pos)] & 1) ? -1 : 0; }
+    __device__ __forceinline__ int op(int axis, int pos) const { return (gf[ge(axis, pos)] & 2) ? 1 : 0; }
+    __device__ __forceinline__ T c(int k, int axis, int pos) const { return ga[k * L::NG + ge(axis, pos)]; }
+};
+
+// Face macroscopic variables from the nine bar distributions of each kind at
+// t+h (Eq. conservedVariable with h, bar for tilde), then the originals of
+// Eq. (original-function) of the six flux-carrying directions of axis A,
+// returned as (xi . e_A) phi_i |S|.
+template <typename T, int A>
+__device__ __forceinline__ void face_tail(const InstDev &I, const T (&fb)[Q], const T (&gb)[Q], const FaceAux<T> &ax,
+                                          bool wall, int side, T area, T (&Ff)[6], T (&Fg)[6])
+{
+    const ParT<T> &Pr = par<T>(I);
+    const T h = Pr.h;
+    T phi = 0, sf = 0, mx = 0, my = 0;
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+        phi += gb[q];
+        sf += fb[q];
+        if (cx(q)) mx += T(cx(q)) * fb[q];
+        if (cy(q)) my += T(cy(q)) * fb[q];
+    }
+    Pt<T> s;
+    s.phi = phi;
+    s.rho = rho_of<T>(I, phi);
+    const T irho = T(1) / s.rho;
+    s.Fx = -phi * ax.gmux + (s.rho - Pr.rho_ref) * Pr.gxa;
+    s.Fy = -phi * ax.gmuy + (s.rho - Pr.rho_ref) * Pr.gya;
+    s.grx = Pr.drho * ax.gphix;
+    s.gry = Pr.drho * ax.gphiy;
+    if (wall) {
+        s.ux = 0;
+        s.uy = 0;
+    } else {
+        // (sum xi f + h/2 c_s^2 F) / (c_s^2 rho)
+        s.ux = (T(3) * mx + T(0.5) * h * s.Fx) * irho;
+        s.uy = (T(3) * my + T(0.5) * h * s.Fy) * irho;
+    }
+    s.p = sf + T(0.5) * h * Cst<T>::cs2 * (s.ux * s.grx + s.uy * s.gry - Pr.gamma * s.rho * Pr.lambda * ax.lapmu);
+    s.mu = ax.mu;
+    s.lapmu = ax.lapmu;
+    s.gpx = ax.gpx;
+    s.gpy = ax.gpy;
+    const T tf = tauf_of<T>(I, phi, s.rho), tg = Pr.tau_g;
+    const PtInv<T> v = pt_inv<T>(I, s);
+    const T r1 = T(1) / (T(2) * tf + h), r2 = T(1) / (T(2) * tg + h);
+    const T a1 = T(2) * tf * r1, b1 = h * r1, c1 = tf * h * r1;
+    const T a2 = T(2) * tg * r2, b2 = h * r2, c2 = tg * h * r2;
+    T fo[Q], go[Q];
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        const int q = fset<A>(k);
+        // at a wall only the outgoing originals are formed; incoming ones bounce back
+        if (wall && ca(q, A) * side < 0) continue;
+        T feq, geq, F1, F2;
+        eq_src<T>(s, v, q, feq, geq, F1, F2);
+        fo[q] = a1 * fb[q] + b1 * feq + c1 * F1;
+        go[q] = a2 * gb[q] + b2 * geq + c2 * F2;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        const int q = fset<A>(k);
+        T vf, vg;
+        if (wall && ca(q, A) * side < 0) {
+            vf = fo[opp(q)];
+            vg = go[opp(q)];
+        } else {
+            vf = fo[q];
+            vg = go[q];
+        }
+        Ff[k] = T(ca(q, A)) * vf * area;
+        Fg[k] = T(ca(q, A)) * vg * area;
+    }
+}
+
+// Flux values of the face between positions a (low side) and b = a + e_A of a
+// tile, or of the wall face of whichever of the two lies in the domain.
+template <typename T, int BX, int BY, int A>
+__device__ __forceinline__ void tile_face(const InstDev &I, const Tile<T, BX, BY> &S, int xa, int ya, T (&Ff)[6],
+                                          T (&Fg)[6])
+{
+    const ParT<T> &Pr = par<T>(I);
+    using TL = Tile<T, BX, BY>;
+    constexpr int A1 = TL::L::A1;
+    const int xb = xa + (A == 0 ? 1 : 0), yb = ya + (A == 1 ? 1 : 0);
+    const int pa = A == 0 ? xa : ya, pb = A == 0 ? xb : yb, pt = A == 0 ? ya : xa;
+#pragma unroll
+    for (int k = 0; k < 6; k++) { Ff[k] = 0; Fg[k] = 0; }
+    if (S.gidx(1 - A, pt) < 0) return;
+    const bool va = S.gidx(A, pa) >= 0, vb = S.gidx(A, pb) >= 0;
+    const T h = Pr.h;
+    const T area = S.c(10, 1 - A, pt);
+    const T te1m = S.c(4, 1 - A, pt), te10 = S.c(5, 1 - A, pt), te1p = S.c(6, 1 - A, pt);
+    const int tstep = A == 0 ? TL::L::W1 : 1;
+    const int tm = S.om(1 - A, pt) * tstep, tp = S.op(1 - A, pt) * tstep;
+    const T *bpf = S.bp;
+    const T *bpg = S.bp + 9 * A1;
+    T fb[Q], gb[Q];
+    FaceAux<T> ax;
+    if (va && vb) {
+        const int ia = TL::i1(xa, ya), ib = TL::i1(xb, yb);
+        const T wL = S.c(7, A, pa), wR = S.c(8, A, pa), invd = S.c(9, A, pa);
+#pragma unroll
+        for (int q = 0; q < Q; q++) {
+#pragma unroll
+            for (int kind = 0; kind < 2; kind++) {
+                const T *B = (kind == 0 ? bpf : bpg) + q * A1;
+                const T bL = B[ia], bR = B[ib];
+                T v = (wL * bL + wR * bR) - h * T(ca(q, A)) * ((bR - bL) * invd);
+                if (ca(q, 1 - A)) {
+                    const T tL = te1m * B[ia + tm] + te10 * bL + te1p * B[ia + tp];
+                    const T tR = te1m * B[ib + tm] + te10 * bR + te1p * B[ib + tp];
+                    v -= h * T(ca(q, 1 - A)) * (wL * tL + wR * tR);
+                }
+                (kind == 0 ? fb : gb)[q] = v;
+            }
+        }
+        const int ma = TL::i3(xa, ya), mb = TL::i3(xb, yb);
+        ax.mu = wL * S.mu[ma] + wR * S.mu[mb];
+        ax.lapmu = wL * S.lmu[ia] + wR * S.lmu[ib];
+        ax.gmux = wL * S.gmx[ia] + wR * S.gmx[ib];
+        ax.gmuy = wL * S.gmy[ia] + wR * S.gmy[ib];
+        ax.gphix = wL * S.gfx[ia] + wR * S.gfx[ib];
+        ax.gphiy = wL * S.gfy[ia] + wR * S.gfy[ib];
+        ax.gpx = wL * S.gpx[ia] + wR * S.gpx[ib];
+        ax.gpy = wL * S.gpy[ia] + wR * S.gpy[ib];
+        face_tail<T, A>(I, fb, gb, ax, false, 0, area, Ff, Fg);
+        return;
+    }
+    int side, xc, yc, pc;
+    if (!va && vb && (S.gf[TL::ge(A, pb)] & 4)) { side = -1; xc = xb; yc = yb; pc = pb; }
+    else if (va && !vb && (S.gf[TL::ge(A, pa)] & 8)) { side = +1; xc = xa; yc = ya; pc = pa; }
+    else return;
+    // wall face of cell c: Taylor reconstruction from the cell centre for the
+    // outgoing and parallel directions, bounce-back for the incoming ones
+    const int ic = TL::i1(xc, yc);
+    const int nstep = A == 0 ? 1 : TL::L::W1;
+    const int nm = S.om(A, pc) * nstep, np = S.op(A, pc) * nstep;
+    const T ne1m = S.c(4, A, pc), ne10 = S.c(5, A, pc), ne1p = S.c(6, A, pc);
+    const T half_d = T(0.5) * S.c(10, A, pc);
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+        if (ca(q, A) * side < 0) continue;
+        const T off = T(side) * half_d - h * T(ca(q, A));
+        const T ht = h * T(ca(q, 1 - A));
+#pragma unroll
+        for (int kind = 0; kind < 2; kind++) {
+            const T *B = (kind == 0 ? bpf : bpg) + q * A1;
+            const T b = B[ic];
+            (kind == 0 ? fb : gb)[q] = b + off * (ne1m * B[ic + nm] + ne10 * b + ne1p * B[ic + np])
+                                     - ht * (te1m * B[ic + tm] + te10 * b + te1p * B[ic + tp]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+        if (ca(q, A) * side < 0) {
+            fb[q] = fb[opp(q)];
+            gb[q] = gb[opp(q)];
+        }
+    }
+    ax.mu = S.mu[TL::i3(xc, yc)];
+    ax.lapmu = S.lmu[ic];
+    ax.gmux = A == 0 ? T(0) : S.gmx[ic];
+    ax.gmuy = A == 1 ? T(0) : S.gmy[ic];
+    ax.gphix = A == 0 ? T(0) : S.gfx[ic];
+    ax.gphiy = A == 1 ? T(0) : S.gfy[ic];
+    ax.gpx = A == 0 ? T(0) : S.gpx[ic];
+    ax.gpy = A == 1 ? T(0) : S.gpy[ic];
+    face_tail<T, A>(I, fb, gb, ax, true, side, area, Ff, Fg);
+}
+
+template <typename T, int BX, int BY, int MINB>
+__global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles,
+                                                       const AxisRecT<T> *__restrict__ geo, StepIO<T> io)
+{
+    using TL = Tile<T, BX, BY>;
+    using L = typename TL::L;
+    extern __shared__ __align__(16) unsigned char smem[];
+    TL S(smem);
+    const int4 t = tiles[blockIdx.x];
+    const InstDev &I = insts[t.x];
+    const ParT<T> &Pr = par<T>(I);
+    if (io.status[t.x]) return;   // masked: non-finite instance of a batch
+    const int i0 = t.y, j0 = t.z;
+    const int tid = threadIdx.y * BX + threadIdx.x;
+    constexpr int NT = BX * BY;
+    const long long N = io.N;
+
+    // ---- geometry of the region columns and rows (SoA)
+    for (int r = tid; r < L::NG; r += NT) {
+        const bool isx = r < L::W4;
+        const int pos = isx ? r - 4 : r - L::W4 - 4;
+        const int n = isx ? I.nx : I.ny;
+        const bool per = (isx ? I.bcx : I.bcy) == 0;
+        int g = (isx ? i0 : j0) + pos;
+        if (per) g = ((g % n) + n) % n;
+        else if (g < 0 || g >= n) g = -1;
+        T v[11];
+        int fl = 0;
+        if (g >= 0) {
+            const AxisRecT<T> &R = geo[(isx ? I.gx_off : I.gy_off) + g];
+            v[0] = R.c1m; v[1] = R.c1p; v[2] = R.c2m; v[3] = R.c2p;
+            v[4] = R.e1m; v[5] = R.e10; v[6] = R.e1p;
+            v[7] = R.wL; v[8] = R.wR; v[9] = R.invd; v[10] = R.d;
+            fl = (R.km == g ? 0 : 1) | (R.kp == g ? 0 : 2) | (R.lo_wall ? 4 : 0) | (R.hi_wall ? 8 : 0);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 11; k++) v[k] = T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < 11; k++) S.ga[k * L::NG + r] = v[k];
+        S.gg[r] = g;
+        S.gf[r] = fl;
+    }
+    __syncthreads();
+    auto cell = [&](int gi, int gj) -> long long { return I.cell0 + (long long)gj * I.nxp + gi; };
+
+    // ---- phase 1: asynchronous copies of phi (R4), then of tilde f (R2) and
+    // tilde g (R1); positions outside the domain are zero-filled
+    for (int r = tid; r < L::A4; r += NT) {
+        const int x = r % L::W4 - 4, y = r / L::W4 - 4;
+        const int gi = S.gidx(0, x), gj = S.gidx(1, y);
+        if (gi >= 0 && gj >= 0) {
+            cp_async<sizeof(phi_t<T>)>(S.phi + r, io.phi_in + cell(gi, gj));
+        } else {
+            phi_t<T> v;
+            phi_from_zero(v);
+            S.phi[r] = v;
+        }
+    }
+    cp_commit();
+    for (int r = tid; r < L::A2; r += NT) {
+        const int x = r % L::W2 - 2, y = r / L::W2 - 2;
+        const int gi = S.gidx(0, x), gj = S.gidx(1, y);
+        if (gi >= 0 && gj >= 0) {
+            const long long c = cell(gi, gj);
+#pragma unroll
+            for (int q = 0; q < Q; q++) cp_async<sizeof(T)>(S.sf + q * L::A2 + r, io.f_in + q * N + c);
+        } else {
+#pragma unroll
+            for (int q = 0; q < Q; q++) S.sf[q * L::A2 + r] = T(0);
+        }
+    }
+    for (int r = tid; r < L::A1; r += NT) {
+        const int x = r % L::W1 - 1, y = r / L::W1 - 1;
+        const int gi = S.gidx(0, x), gj = S.gidx(1, y);
+        if (gi >= 0 && gj >= 0) {
+            const long long c = cell(gi, gj);
+#pragma unroll
+            for (int q = 0; q < Q; q++) cp_async<sizeof(T)>(S.sg + q * L::A1 + r, io.g_in + q * N + c);
+        } else {
+#pragma unroll
+            for (int q = 0; q < Q; q++) S.sg[q * L::A1 + r] = T(0);
+        }
+    }
+    cp_commit();
+    cp_wait<1>();   // phi has landed
+    __syncthreads();
+
+    // ---- phase 2: mu on R3 (Eq. chemicalpotential), differences of the stored phi
+    for (int r = tid; r < L::A3; r += NT) {
+        const int x = r % L::W3 - 3, y = r / L::W3 - 3;
+        T mu = 0;
+        if (S.gidx(0, x) >= 0 && S.gidx(1, y) >= 0) {
+            const phi_t<T> p0 = S.phi[TL::i4(x, y)];
+            const T lap = (S.c(2, 0, x) * phi_sub(S.phi[TL::i4(x + S.om(0, x), y)], p0)
+                         + S.c(3, 0, x) * phi_sub(S.phi[TL::i4(x + S.op(0, x), y)], p0))
+                        + (S.c(2, 1, y) * phi_sub(S.phi[TL::i4(x, y + S.om(1, y))], p0)
+                         + S.c(3, 1, y) * phi_sub(S.phi[TL::i4(x, y + S.op(1, y))], p0));
+            const T dpsi = T(4) * Pr.beta * phi_subc(p0, I.cA)
+                         * phi_subc(p0, I.cB)
+                         * phi_subc(p0, I.cM);
+            mu = dpsi - Pr.kappa * lap;
+        }
+        S.mu[r] = mu;
+    }
+    cp_wait<0>();   // tilde f and g have landed
+    __syncthreads();
+
+    const T hdt = T(0.5) * Pr.dt;
+    const T cs2 = Cst<T>::cs2;
+    // ---- phase 3: p on R2 (Eqs. u, P); needs grad mu, lap mu, grad phi and f~
+    for (int r = tid; r < L::A2; r += NT) {
+        const int x = r % L::W2 - 2, y = r / L::W2 - 2;
+        T vp = 0;
+        if (S.gidx(0, x) >= 0 && S.gidx(1, y) >= 0) {
+            const T m0 = S.mu[TL::i3(x, y)];
+            const T mxm = S.mu[TL::i3(x + S.om(0, x), y)] - m0, mxp = S.mu[TL::i3(x + S.op(0, x), y)] - m0;
+            const T mym = S.mu[TL::i3(x, y + S.om(1, y))] - m0, myp = S.mu[TL::i3(x, y + S.op(1, y))] - m0;
+            const T gmx = S.c(0, 0, x) * mxm + S.c(1, 0, x) * mxp;
+            const T gmy = S.c(0, 1, y) * mym + S.c(1, 1, y) * myp;
+            const T lmu = (S.c(2, 0, x) * mxm + S.c(3, 0, x) * mxp) + (S.c(2, 1, y) * mym + S.c(3, 1, y) * myp);
+            const phi_t<T> p0 = S.phi[TL::i4(x, y)];
+            const T gfx = S.c(0, 0, x) * phi_sub(S.phi[TL::i4(x + S.om(0, x), y)], p0)
+                        + S.c(1, 0, x) * phi_sub(S.phi[TL::i4(x + S.op(0, x), y)], p0);
+            const T gfy = S.c(0, 1, y) * phi_sub(S.phi[TL::i4(x, y + S.om(1, y))], p0)
+                        + S.c(1, 1, y) * phi_sub(S.phi[TL::i4(x, y + S.op(1, y))], p0);
+            const T phi = T(phi_val(p0));
+            const T rho = rho_of<T>(I, phi);
+            const T Fx = -phi * gmx + (rho - Pr.rho_ref) * Pr.gxa;
+            const T Fy = -phi * gmy + (rho - Pr.rho_ref) * Pr.gya;
+            T sf = 0, mx = 0, my = 0;
+#pragma unroll
+            for (int q = 0; q < Q; q++) {
+                const T v = S.sf[q * L::A2 + r];
+                sf += v;
+                if (cx(q)) mx += T(cx(q)) * v;
+                if (cy(q)) my += T(cy(q)) * v;
+            }
+            const T irho = T(1) / rho;
+            const T ux = (T(3) * mx + hdt * Fx) * irho;
+            const T uy = (T(3) * my + hdt * Fy) * irho;
+            vp = sf + hdt * cs2 * (ux * Pr.drho * gfx + uy * Pr.drho * gfy - Pr.gamma * rho * Pr.lambda * lmu);
+        }
+        S.p[r] = vp;
+    }
+    __syncthreads();
+
+    // ---- phase 4: grad p, u and bar-plus of both distributions on R1 (Eq. relations1)
+    const T dt = Pr.dt, h = Pr.h, tg = Pr.tau_g;
+    const T rg = T(1) / (T(2) * tg + dt);
+    const T ag = (T(2) * tg - h) * rg, bg = T(3) * h * rg, cg = T(3) * tg * h * rg;
+    for (int r = tid; r < L::A1; r += NT) {
+        const int x = r % L::W1 - 1, y = r / L::W1 - 1;
+        if (S.gidx(0, x) < 0 || S.gidx(1, y) < 0) {
+            S.gmx[r] = 0; S.gmy[r] = 0; S.lmu[r] = 0; S.gfx[r] = 0; S.gfy[r] = 0; S.gpx[r] = 0; S.gpy[r] = 0;
+#pragma unroll
+            for (int q = 0; q < 2 * Q; q++) S.bp[q * L::A1 + r] = 0;
+            continue;
+        }
+        const int k2 = TL::i2(x, y);
+        const T p0 = S.p[k2];
+        const T gpx = S.c(0, 0, x) * (S.p[TL::i2(x + S.om(0, x), y)] - p0) + S.c(1, 0, x) * (S.p[TL::i2(x + S.op(0, x), y)] - p0);
+        const T gpy = S.c(0, 1, y) * (S.p[TL::i2(x, y + S.om(1, y))] - p0) + S.c(1, 1, y) * (S.p[TL::i2(x, y + S.op(1, y))] - p0);
+        const T m0 = S.mu[TL::i3(x, y)];
+        const T mxm = S.mu[TL::i3(x + S.om(0, x), y)] - m0, mxp = S.mu[TL::i3(x + S.op(0, x), y)] - m0;
+        const T mym = S.mu[TL::i3(x, y + S.om(1, y))] - m0, myp = S.mu[TL::i3(x, y + S.op(1, y))] - m0;
+        const T gmx = S.c(0, 0, x) * mxm + S.c(1, 0, x) * mxp;
+        const T gmy = S.c(0, 1, y) * mym + S.c(1, 1, y) * myp;
+        const T lmu = (S.c(2, 0, x) * mxm + S.c(3, 0, x) * mxp) + (S.c(2, 1, y) * mym + S.c(3, 1, y) * myp);
+        const phi_t<T> ph0 = S.phi[TL::i4(x, y)];
+        const T gfx = S.c(0, 0, x) * phi_sub(S.phi[TL::i4(x + S.om(0, x), y)], ph0)
+                    + S.c(1, 0, x) * phi_sub(S.phi[TL::i4(x + S.op(0, x), y)], ph0);
+        const T gfy = S.c(0, 1, y) * phi_sub(S.phi[TL::i4(x, y + S.om(1, y))], ph0)
+                    + S.c(1, 1, y) * phi_sub(S.phi[TL::i4(x, y + S.op(1, y))], ph0);
+        S.gmx[r] = gmx; S.gmy[r] = gmy; S.lmu[r] = lmu; S.gfx[r] = gfx; S.gfy[r] = gfy; S.gpx[r] = gpx; S.gpy[r] = gpy;
+        T fv[Q];
+        T mx = 0, my = 0;
+#pragma unroll
+        for (int q = 0; q < Q; q++) {
+            fv[q] = S.sf[q * L::A2 + k2];
+            if (cx(q)) mx += T(cx(q)) * fv[q];
+            if (cy(q)) my += T(cy(q)) * fv[q];
+        }
+        Pt<T> s;
+        s.phi = T(phi_val(ph0));
+        s.rho = rho_of<T>(I, s.phi);
+        s.Fx = -s.phi * gmx + (s.rho - Pr.rho_ref) * Pr.gxa;
+        s.Fy = -s.phi * gmy + (s.rho - Pr.rho_ref) * Pr.gya;
+        const T irho = T(1) / s.rho;
+        s.ux = (T(3) * mx + hdt * s.Fx) * irho;
+        s.uy = (T(3) * my + hdt * s.Fy) * irho;
+        s.p = p0;
+        s.mu = m0;
+        s.lapmu = lmu;
+        s.grx = Pr.drho * gfx;
+        s.gry = Pr.drho * gfy;
+        s.gpx = gpx;
+        s.gpy = gpy;
+        const T tf = tauf_of<T>(I, s.phi, s.rho);
+        const T rf = T(1) / (T(2) * tf + dt);
+        const T af = (T(2) * tf - h) * rf, bf = T(3) * h * rf, cf = T(3) * tf * h * rf;
+        const PtInv<T> v = pt_inv<T>(I, s);
+#pragma unroll
+        for (int q = 0; q < Q; q++) {
+            T feq, geq, Ff, Fg;
+            eq_src<T>(s, v, q, feq, geq, Ff, Fg);
+            S.bp[q * L::A1 + r] = af * fv[q] + bf * feq + cf * Ff;
+            S.bp[(Q + q) * L::A1 + r] = ag * S.sg[q * L::A1 + r] + bg * geq + cg * Fg;
+        }
+    }
+    __syncthreads();
+
+    // ---- phase 5: every face of the tile once (x faces first in the index space)
+    for (int k = tid; k < L::NFT; k += NT) {
+        T Ff[6], Fg[6];
+        if (k < L::NFX) tile_face<T, BX, BY, 0>(I, S, k % (BX + 1) - 1, k / (BX + 1), Ff, Fg);
+        else tile_face<T, BX, BY, 1>(I, S, (k - L::NFX) % BX, (k - L::NFX) / BX - 1, Ff, Fg);
+#pragma unroll
+        for (int m = 0; m < 6; m++) { S.flux[m * L::NFT + k] = Ff[m]; S.flux[(6 + m) * L::NFT + k] = Fg[m]; }
+    }
+    __syncthreads();
+
+    // ---- phase 6: update of the tile cell (Eqs. relations2, updatef)
+    const int x = threadIdx.x, y = threadIdx.y;
+    const int gi = i0 + x, gj = j0 + y;
+    if (gi >= I.nx || gj >= I.ny) return;
+    T Jf[Q], Jg[Q];
+    Jf[0] = 0; Jg[0] = 0;
+    {
+        const int kw = y * (BX + 1) + x, ke = kw + 1;                 // west and east faces
+        const int ks = L::NFX + y * BX + x, kn = ks + BX;            // south and north faces
+#pragma unroll
+        for (int q = 1; q < Q; q++) { Jf[q] = 0; Jg[q] = 0; }
+#pragma unroll
+        for (int m = 0; m < 6; m++) {
+            const int qx = xset(m), qy = yset(m);
+            Jf[qx] += S.flux[m * L::NFT + ke] - S.flux[m * L::NFT + kw];
+            Jg[qx] += S.flux[(6 + m) * L::NFT + ke] - S.flux[(6 + m) * L::NFT + kw];
+            Jf[qy] += S.flux[m * L::NFT + kn] - S.flux[m * L::NFT + ks];
+            Jg[qy] += S.flux[(6 + m) * L::NFT + kn] - S.flux[(6 + m) * L::NFT + ks];
+        }
+    }
+    const long long c = cell(gi, gj);
+    const int r1 = TL::i1(x, y), r2 = TL::i2(x, y);
+    const T dtv = dt / (S.c(10, 0, x) * S.c(10, 1, y));
+    bool finite = true;
+    if constexpr (sizeof(T) == sizeof(double)) {
+        T phi = 0;
+#pragma unroll
+        for (int q = 0; q < Q; q++) {
+            const T fn = T(4.0 / 3.0) * S.bp[q * L::A1 + r1] - T(1.0 / 3.0) * S.sf[q * L::A2 + r2] - dtv * Jf[q];
+            const T gn = T(4.0 / 3.0) * S.bp[(Q + q) * L::A1 + r1] - T(1.0 / 3.0) * S.sg[q * L::A1 + r1] - dtv * Jg[q];
+            io.f_out[q * N + c] = fn;
+            io.g_out[q * N + c] = gn;
+            phi += gn;
+            finite = finite && isfinite(fn) && isfinite(gn);
+        }
+        io.phi_out[c] = phi;
+    } else {
+        // sum_i g~+_i = phi exactly, so phi advances by the flux balance alone
+        // (kept as a float pair); the rest distribution g~_0 is rebuilt from it
+        T jsum = 0, gsum = 0;
+#pragma unroll
+        for (int q = 0; q < Q; q++) {
+            const T fn = T(4.0 / 3.0) * S.bp[q * L::A1 + r1] - T(1.0 / 3.0) * S.sf[q * L::A2 + r2] - dtv * Jf[q];
+            io.f_out[q * N + c] = fn;
+            finite = finite && isfinite(fn);
+            jsum += Jg[q];
+            if (q > 0) {
+                const T gn = T(4.0 / 3.0) * S.bp[(Q + q) * L::A1 + r1] - T(1.0 / 3.0) * S.sg[q * L::A1 + r1] - dtv * Jg[q];
+                io.g_out[q * N + c] = gn;
+                gsum += gn;
+                finite = finite && isfinite(gn);
+            }
+        }
+        const phi_t<T> phi = phi_add(io.phi_in[c], -(dtv * jsum));   // an L2 hit: read in phase 1
+        io.phi_out[c] = phi;
+        io.g_out[c] = phi_subt(phi, gsum);
+        finite = finite && isfinite(phi_val(phi));
+    }
+    if (!finite) atomicOr(io.status + t.x, 1);
+}
+
+}  // namespace dugks

@@ -28,27 +28,19 @@ __device__ __forceinline__ long long cell_of(const InstDev &I, int i, int j)
 template <typename T>
 __device__ __forceinline__ T rho_of(const InstDev &I, T phi)
 {
+    const ParT<T> &Pr = par<T>(I);
     // Eq. (oderrho) written as rhoB + (rhoA - rhoB)(phi - phiB)/(phiA - phiB)
-    return T(I.rhoB) + T(I.drho) * (phi - T(I.phiB));
+    return Pr.rhoB + Pr.drho * (phi - Pr.phiB);
 }
 
 template <typename T>
 __device__ __forceinline__ T tauf_of(const InstDev &I, T phi, T rho)
 {
+    const ParT<T> &Pr = par<T>(I);
     // Eq. (mixvis) and tau_f = nu / c_s^2 with nu = mu / rho (Eq. kineticandmobility)
-    T muA = T(I.muA), muB = T(I.muB);
-    T mu = muA * muB * (T(I.phiA) - T(I.phiB)) / ((phi - T(I.phiB)) * muB + (T(I.phiA) - phi) * muA);
+    T muA = Pr.muA, muB = Pr.muB;
+    T mu = muA * muB * (Pr.phiA - Pr.phiB) / ((phi - Pr.phiB) * muB + (Pr.phiA - phi) * muA);
     return mu / (rho * Cst<T>::cs2);
-}
-
-// s_i(u) of Eq. (su)
-template <typename T>
-__device__ __forceinline__ T s_of(int q, T ux, T uy)
-{
-    T xu = T(cx(q)) * ux + T(cy(q)) * uy;
-    T uu = ux * ux + uy * uy;
-    const T cs2 = Cst<T>::cs2;
-    return T(wq(q)) * (xu / cs2 + xu * xu / (T(2) * cs2 * cs2) - uu / (T(2) * cs2));
 }
 
 // Point state from which equilibria and sources follow.
@@ -57,22 +49,58 @@ struct Pt {
     T phi, rho, ux, uy, p, mu, lapmu, Fx, Fy, grx, gry, gpx, gpy, tauf;
 };
 
-// f^eq_q, g^eq_q (Eqs. feq, geq, Hi) and F^f_q, F^g_q (Eqs. F, G)
+// Per-point factors shared by the nine directions.  With c_s^2 = 1/3 the
+// divisions of Eq. (su) become the exact multipliers 3, 4.5 and 1.5.
+template <typename T>
+struct PtInv {
+    T uu15;    // u.u / (2 c_s^2)
+    T prho;    // c_s^2 rho
+    T emu;     // eta mu
+    T srcF;    // c_s^2 rho gamma lambda lap(mu)
+    T fg;      // phi / (c_s^2 rho)
+    T Gx, Gy;  // F - grad p
+    T cgx, cgy;  // c_s^2 grad rho
+};
+
+template <typename T>
+__device__ __forceinline__ PtInv<T> pt_inv(const InstDev &I, const Pt<T> &s)
+{
+    const ParT<T> &Pr = par<T>(I);
+    const T cs2 = Cst<T>::cs2;
+    PtInv<T> v;
+    v.uu15 = T(1.5) * (s.ux * s.ux + s.uy * s.uy);
+    v.prho = cs2 * s.rho;
+    v.emu = Pr.eta * s.mu;
+    v.srcF = cs2 * s.rho * Pr.gamma * Pr.lambda * s.lapmu;
+    v.fg = T(3) * s.phi / s.rho;
+    v.Gx = s.Fx - s.gpx;
+    v.Gy = s.Fy - s.gpy;
+    v.cgx = cs2 * s.grx;
+    v.cgy = cs2 * s.gry;
+    return v;
+}
+
+// f^eq_q, g^eq_q (Eqs. feq, geq, su, Hi) and F^f_q, F^g_q (Eqs. F, G)
+template <typename T>
+__device__ __forceinline__ void eq_src(const Pt<T> &s, const PtInv<T> &v, int q, T &feq, T &geq, T &Ff, T &Fg)
+{
+    const T w = T(wq(q));
+    const T xu = T(cx(q)) * s.ux + T(cy(q)) * s.uy;
+    const T si = w * (T(3) * xu + T(4.5) * xu * xu - v.uu15);
+    feq = w * s.p + v.prho * si;
+    const T H = (q == 0) ? s.phi - (T(1) - w) * v.emu : w * v.emu;
+    geq = H + s.phi * si;
+    const T G = w + si;
+    const T ex = T(cx(q)) - s.ux, ey = T(cy(q)) - s.uy;
+    Ff = ex * (s.Fx * G + si * v.cgx) + ey * (s.Fy * G + si * v.cgy) - w * v.srcF;
+    Fg = v.fg * (ex * v.Gx + ey * v.Gy) * G;
+}
+
+// compatibility wrapper: equilibria and sources of one direction
 template <typename T>
 __device__ __forceinline__ void eq_src(const InstDev &I, const Pt<T> &s, int q, T &feq, T &geq, T &Ff, T &Fg)
 {
-    const T cs2 = Cst<T>::cs2;
-    T si = s_of<T>(q, s.ux, s.uy);
-    T w = T(wq(q));
-    T emu = T(I.eta) * s.mu;
-    feq = w * s.p + cs2 * s.rho * si;
-    T H = (q == 0) ? s.phi - (T(1) - w) * emu : w * emu;
-    geq = H + s.phi * si;
-    T G = w + si;
-    T ex = T(cx(q)) - s.ux, ey = T(cy(q)) - s.uy;
-    Ff = ex * (s.Fx * G + si * cs2 * s.grx) + ey * (s.Fy * G + si * cs2 * s.gry)
-       - w * cs2 * s.rho * T(I.gamma) * T(I.lambda) * s.lapmu;
-    Fg = s.phi / (cs2 * s.rho) * (ex * (s.Fx - s.gpx) + ey * (s.Fy - s.gpy)) * G;
+    eq_src<T>(s, pt_inv<T>(I, s), q, feq, geq, Ff, Fg);
 }
 
 // ---------------------------------------------------------------------------
@@ -85,20 +113,22 @@ __global__ void __launch_bounds__(TX *TY) k_mu(const InstDev *__restrict__ insts
 {
     const int4 t = tiles[blockIdx.x];
     const InstDev &I = insts[t.x];
+    const ParT<T> &Pr = par<T>(I);
     if (P.status[t.x]) return;   // masked: non-finite instance of a batch
     const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
     if (i >= I.nx || j >= I.ny) return;
     const AxisRec &ax = geo[I.gx_off + i];
     const AxisRec &ay = geo[I.gy_off + j];
     const long long c = cell_of(I, i, j);
-    // Differences are formed in FP64 and only then rounded to T, so that the
-    // Laplacian of the FP64 order parameter keeps its precision in FP32 mode
-    // (the stencil weights sum to zero: c2m + c20 + c2p = 0).
-    const double p0 = P.phi[c];
-    T lap = (T(ax.c2m) * T(P.phi[cell_of(I, ax.km, j)] - p0) + T(ax.c2p) * T(P.phi[cell_of(I, ax.kp, j)] - p0))
-          + (T(ay.c2m) * T(P.phi[cell_of(I, i, ay.km)] - p0) + T(ay.c2p) * T(P.phi[cell_of(I, i, ay.kp)] - p0));
-    T dpsi = T(4) * T(I.beta) * T(p0 - I.phiA) * T(p0 - I.phiB) * T(p0 - 0.5 * (I.phiA + I.phiB));
-    P.mu[c] = dpsi - T(I.kappa) * lap;
+    // Differences of the stored phi are formed first, so that the Laplacian
+    // keeps the precision of the stored phi in FP32 mode (the stencil weights
+    // sum to zero: c2m + c20 + c2p = 0).
+    const phi_t<T> p0 = P.phi[c];
+    T lap = (T(ax.c2m) * phi_sub(P.phi[cell_of(I, ax.km, j)], p0) + T(ax.c2p) * phi_sub(P.phi[cell_of(I, ax.kp, j)], p0))
+          + (T(ay.c2m) * phi_sub(P.phi[cell_of(I, i, ay.km)], p0) + T(ay.c2p) * phi_sub(P.phi[cell_of(I, i, ay.kp)], p0));
+    T dpsi = T(4) * Pr.beta * phi_subc(p0, I.cA) * phi_subc(p0, I.cB)
+           * phi_subc(p0, I.cM);
+    P.mu[c] = dpsi - Pr.kappa * lap;
 }
 
 // first derivatives of a cell field along x and y (mirror ghosts)
@@ -110,13 +140,13 @@ __device__ __forceinline__ void grad_field(const InstDev &I, const T *__restrict
     gy = T(ay.c1m) * F[cell_of(I, i, ay.km)] + T(ay.c10) * f0 + T(ay.c1p) * F[cell_of(I, i, ay.kp)];
 }
 
-// first derivatives of the FP64 order parameter, difference form (weights sum to zero)
+// first derivatives of the stored order parameter, difference form (weights sum to zero)
 template <typename T>
-__device__ __forceinline__ void grad_phi(const InstDev &I, const double *__restrict__ F, const AxisRec &ax,
-                                         const AxisRec &ay, int i, int j, double f0, T &gx, T &gy)
+__device__ __forceinline__ void grad_phi(const InstDev &I, const phi_t<T> *__restrict__ F, const AxisRec &ax,
+                                         const AxisRec &ay, int i, int j, phi_t<T> f0, T &gx, T &gy)
 {
-    gx = T(ax.c1m) * T(F[cell_of(I, ax.km, j)] - f0) + T(ax.c1p) * T(F[cell_of(I, ax.kp, j)] - f0);
-    gy = T(ay.c1m) * T(F[cell_of(I, i, ay.km)] - f0) + T(ay.c1p) * T(F[cell_of(I, i, ay.kp)] - f0);
+    gx = T(ax.c1m) * phi_sub(F[cell_of(I, ax.km, j)], f0) + T(ax.c1p) * phi_sub(F[cell_of(I, ax.kp, j)], f0);
+    gy = T(ay.c1m) * phi_sub(F[cell_of(I, i, ay.km)], f0) + T(ay.c1p) * phi_sub(F[cell_of(I, i, ay.kp)], f0);
 }
 
 // ---------------------------------------------------------------------------
@@ -129,6 +159,7 @@ __global__ void __launch_bounds__(TX *TY) k_macro(const InstDev *__restrict__ in
 {
     const int4 t = tiles[blockIdx.x];
     const InstDev &I = insts[t.x];
+    const ParT<T> &Pr = par<T>(I);
     if (P.status[t.x]) return;   // masked: non-finite instance of a batch
     const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
     if (i >= I.nx || j >= I.ny) return;
@@ -137,15 +168,15 @@ __global__ void __launch_bounds__(TX *TY) k_macro(const InstDev *__restrict__ in
     const long long c = cell_of(I, i, j);
     const long long N = P.N;
     const T cs2 = Cst<T>::cs2;
-    const T phi = T(P.phi[c]), mu = P.mu[c];
+    const T phi = T(phi_val(P.phi[c])), mu = P.mu[c];
     T gmx, gmy, gfx, gfy;
     grad_field(I, P.mu, ax, ay, i, j, mu, gmx, gmy);
-    grad_phi(I, P.phi, ax, ay, i, j, P.phi[c], gfx, gfy);
+    grad_phi<T>(I, P.phi, ax, ay, i, j, P.phi[c], gfx, gfy);
     T lmu = (T(ax.c2m) * P.mu[cell_of(I, ax.km, j)] + T(ax.c20) * mu + T(ax.c2p) * P.mu[cell_of(I, ax.kp, j)])
           + (T(ay.c2m) * P.mu[cell_of(I, i, ay.km)] + T(ay.c20) * mu + T(ay.c2p) * P.mu[cell_of(I, i, ay.kp)]);
     T rho = rho_of<T>(I, phi);
-    T Fx = -phi * gmx + (rho - T(I.rho_ref)) * T(I.gxa);
-    T Fy = -phi * gmy + (rho - T(I.rho_ref)) * T(I.gya);
+    T Fx = -phi * gmx + (rho - Pr.rho_ref) * Pr.gxa;
+    T Fy = -phi * gmy + (rho - Pr.rho_ref) * Pr.gya;
     T sf = 0, mx = 0, my = 0;
 #pragma unroll
     for (int q = 0; q < Q; q++) {
@@ -154,11 +185,11 @@ __global__ void __launch_bounds__(TX *TY) k_macro(const InstDev *__restrict__ in
         if (cx(q)) mx += T(cx(q)) * v;
         if (cy(q)) my += T(cy(q)) * v;
     }
-    T hdt = T(0.5) * T(I.dt);
+    T hdt = T(0.5) * Pr.dt;
     T ux = (mx + hdt * cs2 * Fx) / (cs2 * rho);
     T uy = (my + hdt * cs2 * Fy) / (cs2 * rho);
-    T grx = T(I.drho) * gfx, gry = T(I.drho) * gfy;
-    T p = sf + hdt * cs2 * (ux * grx + uy * gry - T(I.gamma) * rho * T(I.lambda) * lmu);
+    T grx = Pr.drho * gfx, gry = Pr.drho * gfy;
+    T p = sf + hdt * cs2 * (ux * grx + uy * gry - Pr.gamma * rho * Pr.lambda * lmu);
     P.gmux[c] = gmx;
     P.gmuy[c] = gmy;
     P.lapmu[c] = lmu;
@@ -173,7 +204,8 @@ __global__ void __launch_bounds__(TX *TY) k_macro(const InstDev *__restrict__ in
 template <typename T>
 __device__ __forceinline__ void cell_point(const InstDev &I, const Planes<T> &P, long long c, T gpx, T gpy, Pt<T> &s)
 {
-    s.phi = T(P.phi[c]);
+    const ParT<T> &Pr = par<T>(I);
+    s.phi = T(phi_val(P.phi[c]));
     s.rho = rho_of<T>(I, s.phi);
     s.ux = P.ux[c];
     s.uy = P.uy[c];
@@ -181,10 +213,10 @@ __device__ __forceinline__ void cell_point(const InstDev &I, const Planes<T> &P,
     s.mu = P.mu[c];
     s.lapmu = P.lapmu[c];
     T gmx = P.gmux[c], gmy = P.gmuy[c];
-    s.Fx = -s.phi * gmx + (s.rho - T(I.rho_ref)) * T(I.gxa);
-    s.Fy = -s.phi * gmy + (s.rho - T(I.rho_ref)) * T(I.gya);
-    s.grx = T(I.drho) * P.gphix[c];
-    s.gry = T(I.drho) * P.gphiy[c];
+    s.Fx = -s.phi * gmx + (s.rho - Pr.rho_ref) * Pr.gxa;
+    s.Fy = -s.phi * gmy + (s.rho - Pr.rho_ref) * Pr.gya;
+    s.grx = Pr.drho * P.gphix[c];
+    s.gry = Pr.drho * P.gphiy[c];
     s.gpx = gpx;
     s.gpy = gpy;
     s.tauf = tauf_of<T>(I, s.phi, s.rho);
@@ -200,6 +232,7 @@ __global__ void __launch_bounds__(TX *TY) k_cell(const InstDev *__restrict__ ins
 {
     const int4 t = tiles[blockIdx.x];
     const InstDev &I = insts[t.x];
+    const ParT<T> &Pr = par<T>(I);
     if (P.status[t.x]) return;   // masked: non-finite instance of a batch
     const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
     if (i >= I.nx || j >= I.ny) return;
@@ -213,7 +246,7 @@ __global__ void __launch_bounds__(TX *TY) k_cell(const InstDev *__restrict__ ins
     P.gpy[c] = gpy;
     Pt<T> s;
     cell_point(I, P, c, gpx, gpy, s);
-    const T dt = T(I.dt), h = T(I.h), tg = T(I.tau_g), tf = s.tauf;
+    const T dt = Pr.dt, h = Pr.h, tg = Pr.tau_g, tf = s.tauf;
     // Eq. (relations1) coefficients
     const T af = (T(2) * tf - h) / (T(2) * tf + dt), bf = T(3) * h / (T(2) * tf + dt), cf = T(3) * tf * h / (T(2) * tf + dt);
     const T ag = (T(2) * tg - h) / (T(2) * tg + dt), bg = T(3) * h / (T(2) * tg + dt), cg = T(3) * tg * h / (T(2) * tg + dt);
@@ -238,8 +271,9 @@ template <typename T>
 __device__ __forceinline__ void face_originals(const InstDev &I, const T (&fb)[Q], const T (&gb)[Q],
                                                const FaceAux<T> &ax, bool wall, T (&fo)[Q], T (&go)[Q])
 {
+    const ParT<T> &Pr = par<T>(I);
     const T cs2 = Cst<T>::cs2;
-    const T h = T(I.h);
+    const T h = Pr.h;
     T phi = 0, sf = 0, mx = 0, my = 0;
 #pragma unroll
     for (int q = 0; q < Q; q++) {
@@ -251,10 +285,10 @@ __device__ __forceinline__ void face_originals(const InstDev &I, const T (&fb)[Q
     Pt<T> s;
     s.phi = phi;
     s.rho = rho_of<T>(I, phi);
-    s.Fx = -phi * ax.gmux + (s.rho - T(I.rho_ref)) * T(I.gxa);
-    s.Fy = -phi * ax.gmuy + (s.rho - T(I.rho_ref)) * T(I.gya);
-    s.grx = T(I.drho) * ax.gphix;
-    s.gry = T(I.drho) * ax.gphiy;
+    s.Fx = -phi * ax.gmux + (s.rho - Pr.rho_ref) * Pr.gxa;
+    s.Fy = -phi * ax.gmuy + (s.rho - Pr.rho_ref) * Pr.gya;
+    s.grx = Pr.drho * ax.gphix;
+    s.gry = Pr.drho * ax.gphiy;
     if (wall) {
         s.ux = 0;
         s.uy = 0;
@@ -262,13 +296,13 @@ __device__ __forceinline__ void face_originals(const InstDev &I, const T (&fb)[Q
         s.ux = (mx + T(0.5) * h * cs2 * s.Fx) / (cs2 * s.rho);
         s.uy = (my + T(0.5) * h * cs2 * s.Fy) / (cs2 * s.rho);
     }
-    s.p = sf + T(0.5) * h * cs2 * (s.ux * s.grx + s.uy * s.gry - T(I.gamma) * s.rho * T(I.lambda) * ax.lapmu);
+    s.p = sf + T(0.5) * h * cs2 * (s.ux * s.grx + s.uy * s.gry - Pr.gamma * s.rho * Pr.lambda * ax.lapmu);
     s.mu = ax.mu;
     s.lapmu = ax.lapmu;
     s.gpx = ax.gpx;
     s.gpy = ax.gpy;
     s.tauf = tauf_of<T>(I, phi, s.rho);
-    const T tf = s.tauf, tg = T(I.tau_g);
+    const T tf = s.tauf, tg = Pr.tau_g;
     const T a1 = T(2) * tf / (T(2) * tf + h), b1 = h / (T(2) * tf + h), c1 = tf * h / (T(2) * tf + h);
     const T a2 = T(2) * tg / (T(2) * tg + h), b2 = h / (T(2) * tg + h), c2 = tg * h / (T(2) * tg + h);
 #pragma unroll
@@ -286,6 +320,7 @@ template <typename T, int A>
 __device__ void interior_face(const InstDev &I, const Planes<T> &P, const AxisRec *__restrict__ geo, int iL, int jL,
                               int iR, int jR, T (&fo)[Q], T (&go)[Q])
 {
+    const ParT<T> &Pr = par<T>(I);
     const long long N = P.N;
     const AxisRec &rn = (A == 0) ? geo[I.gx_off + iL] : geo[I.gy_off + jL];
     const AxisRec &rt = (A == 0) ? geo[I.gy_off + jL] : geo[I.gx_off + iL];
@@ -300,7 +335,7 @@ __device__ void interior_face(const InstDev &I, const Planes<T> &P, const AxisRe
         cLm = cell_of(I, rt.km, jL); cLp = cell_of(I, rt.kp, jL);
         cRm = cell_of(I, rt.km, jR); cRp = cell_of(I, rt.kp, jR);
     }
-    const T h = T(I.h);
+    const T h = Pr.h;
     T fb[Q], gb[Q];
 #pragma unroll
     for (int q = 0; q < Q; q++) {
@@ -335,6 +370,7 @@ template <typename T, int A>
 __device__ void wall_face(const InstDev &I, const Planes<T> &P, const AxisRec *__restrict__ geo, int i, int j,
                           int side, T (&fo)[Q], T (&go)[Q])
 {
+    const ParT<T> &Pr = par<T>(I);
     const long long N = P.N;
     const AxisRec &rn = (A == 0) ? geo[I.gx_off + i] : geo[I.gy_off + j];
     const AxisRec &rt = (A == 0) ? geo[I.gy_off + j] : geo[I.gx_off + i];
@@ -347,7 +383,7 @@ __device__ void wall_face(const InstDev &I, const Planes<T> &P, const AxisRec *_
         cnm = cell_of(I, i, rn.km); cnp = cell_of(I, i, rn.kp);
         ctm = cell_of(I, rt.km, j); ctp = cell_of(I, rt.kp, j);
     }
-    const T h = T(I.h), half_d = T(0.5) * T(rn.d);
+    const T h = Pr.h, half_d = T(0.5) * T(rn.d);
     const T nm = T(rn.e1m), n0 = T(rn.e10), np = T(rn.e1p);
     const T tm = T(rt.e1m), t0 = T(rt.e10), tp = T(rt.e1p);
     T fb[Q], gb[Q];
@@ -400,6 +436,7 @@ __global__ void __launch_bounds__(TX *TY) k_face(const InstDev *__restrict__ ins
 {
     const int4 t = tiles[blockIdx.x];
     const InstDev &I = insts[t.x];
+    const ParT<T> &Pr = par<T>(I);
     if (P.status[t.x]) return;   // masked: non-finite instance of a batch
     const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
     if (i >= I.nx || j >= I.ny) return;
@@ -433,7 +470,7 @@ __global__ void __launch_bounds__(TX *TY) k_face(const InstDev *__restrict__ ins
 #pragma unroll
     for (int q = 0; q < Q; q++) if (cy(q)) { Jf[q] += T(cy(q)) * fo[q] * ax_area; Jg[q] += T(cy(q)) * go[q] * ax_area; }
 
-    const T dtv = T(I.dt) / (ax_area * ay_area);
+    const T dtv = Pr.dt / (ax_area * ay_area);
     bool finite = true;
     if constexpr (sizeof(T) == sizeof(double)) {
         T phi = 0;
@@ -465,10 +502,10 @@ __global__ void __launch_bounds__(TX *TY) k_face(const InstDev *__restrict__ ins
                 finite = finite && isfinite(gn);
             }
         }
-        const double phi = P.phi[c] - (double)(dtv * jsum);
+        const phi_t<T> phi = phi_add(P.phi[c], -(dtv * jsum));
         P.phi[c] = phi;
-        P.g[c] = T(phi - (double)gsum);
-        finite = finite && isfinite(phi);
+        P.g[c] = phi_subt(phi, gsum);
+        finite = finite && isfinite(phi_val(phi));
     }
     if (!finite) atomicOr(P.status + t.x, 1);
 }
@@ -483,6 +520,7 @@ __global__ void __launch_bounds__(TX *TY) k_init(const InstDev *__restrict__ ins
 {
     const int4 t = tiles[blockIdx.x];
     const InstDev &I = insts[t.x];
+    const ParT<T> &Pr = par<T>(I);
     const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
     if (i >= I.nx || j >= I.ny) return;
     const AxisRec &ax = geo[I.gx_off + i];
@@ -490,7 +528,7 @@ __global__ void __launch_bounds__(TX *TY) k_init(const InstDev *__restrict__ ins
     const long long c = cell_of(I, i, j);
     const long long N = P.N;
     Pt<T> s;
-    s.phi = T(P.phi[c]);
+    s.phi = T(phi_val(P.phi[c]));
     s.rho = rho_of<T>(I, s.phi);
     s.ux = P.ux[c];
     s.uy = P.uy[c];
@@ -498,18 +536,18 @@ __global__ void __launch_bounds__(TX *TY) k_init(const InstDev *__restrict__ ins
     s.mu = P.mu[c];
     T gmx, gmy, gfx, gfy, gpx, gpy;
     grad_field(I, P.mu, ax, ay, i, j, s.mu, gmx, gmy);
-    grad_phi(I, P.phi, ax, ay, i, j, P.phi[c], gfx, gfy);
+    grad_phi<T>(I, P.phi, ax, ay, i, j, P.phi[c], gfx, gfy);
     grad_field(I, P.p, ax, ay, i, j, s.p, gpx, gpy);
     s.lapmu = (T(ax.c2m) * P.mu[cell_of(I, ax.km, j)] + T(ax.c20) * s.mu + T(ax.c2p) * P.mu[cell_of(I, ax.kp, j)])
             + (T(ay.c2m) * P.mu[cell_of(I, i, ay.km)] + T(ay.c20) * s.mu + T(ay.c2p) * P.mu[cell_of(I, i, ay.kp)]);
-    s.Fx = -s.phi * gmx + (s.rho - T(I.rho_ref)) * T(I.gxa);
-    s.Fy = -s.phi * gmy + (s.rho - T(I.rho_ref)) * T(I.gya);
-    s.grx = T(I.drho) * gfx;
-    s.gry = T(I.drho) * gfy;
+    s.Fx = -s.phi * gmx + (s.rho - Pr.rho_ref) * Pr.gxa;
+    s.Fy = -s.phi * gmy + (s.rho - Pr.rho_ref) * Pr.gya;
+    s.grx = Pr.drho * gfx;
+    s.gry = Pr.drho * gfy;
     s.gpx = gpx;
     s.gpy = gpy;
     s.tauf = tauf_of<T>(I, s.phi, s.rho);
-    const T hdt = T(0.5) * T(I.dt);
+    const T hdt = T(0.5) * Pr.dt;
     bool finite = true;
     T gsum = 0;
 #pragma unroll
@@ -522,8 +560,8 @@ __global__ void __launch_bounds__(TX *TY) k_init(const InstDev *__restrict__ ins
         if (q > 0) gsum += gv;
         finite = finite && isfinite(fv) && isfinite(gv);
     }
-    // FP32 storage: the rest distribution is rebuilt from the FP64 phi (sum g = phi)
-    if constexpr (sizeof(T) != sizeof(double)) P.g[c] = T(P.phi[c] - (double)gsum);
+    // FP32 storage: the rest distribution is rebuilt from the stored phi (sum g = phi)
+    if constexpr (sizeof(T) != sizeof(double)) P.g[c] = phi_subt(P.phi[c], gsum);
     if (!finite) atomicOr(P.status + t.x, 1);
 }
 
@@ -534,13 +572,14 @@ __global__ void __launch_bounds__(TX *TY) k_phi(const InstDev *__restrict__ inst
 {
     const int4 t = tiles[blockIdx.x];
     const InstDev &I = insts[t.x];
+    const ParT<T> &Pr = par<T>(I);
     const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
     if (i >= I.nx || j >= I.ny) return;
     const long long c = cell_of(I, i, j);
     double phi = 0;
 #pragma unroll
     for (int q = 0; q < Q; q++) phi += (double)P.g[q * P.N + c];
-    P.phi[c] = phi;
+    phi_from_double(phi, P.phi[c]);
 }
 
 // ---------------------------------------------------------------------------
@@ -554,11 +593,12 @@ __global__ void __launch_bounds__(TX *TY) k_reduce(const InstDev *__restrict__ i
     __shared__ double2 red[TX * TY / 32];
     const int4 t = tiles[blockIdx.x];
     const InstDev &I = insts[t.x];
+    const ParT<T> &Pr = par<T>(I);
     const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
     double a = 0.0, b = 0.0;
     if (i < I.nx && j < I.ny) {
         const long long c = cell_of(I, i, j);
-        const double phi = P.phi[c];
+        const double phi = phi_to_double(P.phi[c]);
         double vol = geo[I.gx_off + i].d * geo[I.gy_off + j].d;
         a = vol * phi;
         b = vol * (I.rhoB + I.drho * (phi - I.phiB));
@@ -591,6 +631,29 @@ __global__ void k_reduce_inst(const InstDev *__restrict__ insts, int n_inst, con
     out[k] = s;
 }
 
+// Gather the stored phi plane into a dense double array and back.
+template <typename S>
+__global__ void k_pack_phi(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles, const S *__restrict__ src,
+                           double *__restrict__ dst, const long long *__restrict__ dense0)
+{
+    const int4 t = tiles[blockIdx.x];
+    const InstDev &I = insts[t.x];
+    const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
+    if (i >= I.nx || j >= I.ny) return;
+    dst[dense0[t.x] + (long long)j * I.nx + i] = phi_to_double(src[cell_of(I, i, j)]);
+}
+
+template <typename S>
+__global__ void k_unpack_phi(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles,
+                             const double *__restrict__ src, S *__restrict__ dst, const long long *__restrict__ dense0)
+{
+    const int4 t = tiles[blockIdx.x];
+    const InstDev &I = insts[t.x];
+    const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
+    if (i >= I.nx || j >= I.ny) return;
+    phi_from_double(src[dense0[t.x] + (long long)j * I.nx + i], dst[cell_of(I, i, j)]);
+}
+
 // Gather a padded plane (type T) into a dense double array and back.
 template <typename T>
 __global__ void k_pack(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles, const T *__restrict__ src,
@@ -598,6 +661,7 @@ __global__ void k_pack(const InstDev *__restrict__ insts, const int4 *__restrict
 {
     const int4 t = tiles[blockIdx.x];
     const InstDev &I = insts[t.x];
+    const ParT<T> &Pr = par<T>(I);
     const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
     if (i >= I.nx || j >= I.ny) return;
     dst[dense0[t.x] + (long long)j * I.nx + i] = (double)src[cell_of(I, i, j)];
@@ -609,6 +673,7 @@ __global__ void k_unpack(const InstDev *__restrict__ insts, const int4 *__restri
 {
     const int4 t = tiles[blockIdx.x];
     const InstDev &I = insts[t.x];
+    const ParT<T> &Pr = par<T>(I);
     const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
     if (i >= I.nx || j >= I.ny) return;
     dst[cell_of(I, i, j)] = (T)src[dense0[t.x] + (long long)j * I.nx + i];

@@ -98,7 +98,7 @@ def load(build_if_missing: bool = True):
     return L
 
 
-NUM_KERNELS = 6
+NUM_KERNELS = 7
 
 
 def _check(fn, rc):

@@ -153,3 +153,20 @@ def test_invalid_init_input_rejected():
     phi[3, 3] = math.nan
     with pytest.raises(dugks.NonFiniteError):
         s.init(phi)
+
+
+@pytest.mark.parametrize("prec", [dugks.FP64, dugks.FP32])
+def test_fused_step_matches_four_kernel_step(prec, monkeypatch):
+    """The one-launch tiled step and the four-kernel step compute the same scheme."""
+    cases = [CASES[0][1], CASES[3][1], CASES[2][1], CASES[5][1]]
+    a = dugks.Sim([c.mesh for c in cases], [c.params for c in cases], prec)
+    monkeypatch.setenv("DUGKS_UNFUSED", "1")
+    b = dugks.Sim([c.mesh for c in cases], [c.params for c in cases], prec)
+    monkeypatch.delenv("DUGKS_UNFUSED")
+    for s in (a, b):
+        s.init([c.phi0 for c in cases])
+        s.step(30)
+    fa, ga = a.state()
+    fb, gb = b.state()
+    tol = 1e-11 if prec == dugks.FP64 else 2e-5
+    assert normwise(fa, fb) < tol and normwise(ga, gb) < tol
