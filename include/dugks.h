@@ -141,6 +141,30 @@ int dugks_kernel_bytes_per_cell(const dugks_sim *sim, int k, double *bytes);
 
 const char *dugks_status_str(int status);
 
+/* Allocation-free FP64 conservation sums of one mesh.  The paper has no
+   counterpart; this exists for callers that cannot allocate device memory,
+   such as a host loop under a device-memory budget owned by another allocator
+   (a cudaMalloc there can fail or fragment that allocator's pool) or a
+   latency-critical loop that cannot accept the device synchronisation of
+   cudaMalloc/cudaFree.
+   Inputs, all device pointers owned by the caller: phi[ny][nx] (dense, x
+   fastest), dx[nx], dy[ny]; phiA, phiB, rhoA, rhoB as in dugks_params.
+   Output: out[0] = sum |V| phi, out[1] = sum |V| rho(phi) (device pointer to
+   two doubles), written on cuda_stream (NULL = legacy default stream).
+   The call allocates nothing: its scratch (one partial pair per 4096 cells) is
+   a file-scope device array of DUGKS_STATIC_MAX_CELLS / 4096 pairs (64 KiB)
+   that every GPU loading this library holds until the process exits.  Meshes
+   with more than DUGKS_STATIC_MAX_CELLS cells are rejected with DUGKS_ERR_ARG
+   before any device work.  The first call on a device looks up the scratch
+   array's device address (cudaGetSymbolAddress, with that device current);
+   make that first call before any stream capture.  Every call overwrites the
+   scratch slots it uses, so no state carries over, but all calls share the one
+   array: calls whose kernels overlap on the GPU (different streams, or
+   different host threads) race and must be serialised by the caller. */
+#define DUGKS_STATIC_MAX_CELLS 16777216
+int dugks_conservation_static(const double *phi, const double *dx, const double *dy, int nx, int ny, double phiA,
+                              double phiB, double rhoA, double rhoB, double *out, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -51,7 +51,8 @@ _lib = None
 EXPORTS = ("dugks_create", "dugks_batch_create", "dugks_destroy", "dugks_init", "dugks_step", "dugks_moments",
            "dugks_conservation", "dugks_batch_status", "dugks_dt", "dugks_info", "dugks_save", "dugks_load",
            "dugks_launch_count", "dugks_set_timing", "dugks_kernel_times", "dugks_kernel_name",
-           "dugks_kernel_bytes_per_cell", "dugks_status_str")
+           "dugks_kernel_bytes_per_cell", "dugks_status_str", "dugks_conservation_static")
+STATIC_MAX_CELLS = 16777216
 
 
 def library_path():
@@ -89,6 +90,7 @@ def load(build_if_missing: bool = True):
     L.dugks_kernel_name.argtypes = [ip]
     L.dugks_kernel_name.restype = ctypes.c_char_p
     L.dugks_kernel_bytes_per_cell.argtypes = [vp, ip, dp]
+    L.dugks_conservation_static.argtypes = [vp, vp, vp, ip, ip] + [ctypes.c_double] * 4 + [vp, vp]
     L.dugks_status_str.argtypes = [ip]
     L.dugks_status_str.restype = ctypes.c_char_p
     for n in EXPORTS:
@@ -251,6 +253,16 @@ class Sim:
         v = ctypes.c_double()
         _check("dugks_kernel_bytes_per_cell", load().dugks_kernel_bytes_per_cell(self.h, int(k), ctypes.byref(v)))
         return v.value
+
+
+def conservation_static(phi_ptr, dx_ptr, dy_ptr, nx, ny, params, out_ptr, stream=0):
+    """Allocation-free conservation sums of one mesh from caller-owned device
+    buffers (raw device addresses): phi[ny][nx], dx[nx], dy[ny] in, out[2] out.
+    Returns the status code (0 on success) without raising."""
+    return load().dugks_conservation_static(ctypes.c_void_p(int(phi_ptr)), ctypes.c_void_p(int(dx_ptr)),
+                                            ctypes.c_void_p(int(dy_ptr)), int(nx), int(ny), params.phiA,
+                                            params.phiB, params.rhoA, params.rhoB, ctypes.c_void_p(int(out_ptr)),
+                                            ctypes.c_void_p(int(stream)))
 
 
 def kernel_name(k):
