@@ -203,7 +203,7 @@ template <typename T>
 int launch_fused(dugks_sim *s)
 {
     using L = FusedLayout<T, TX, TY>;
-    constexpr int MINB = sizeof(T) == 4 ? 2 : 1;   // resident CTAs per SM the registers are sized for
+    constexpr int MINB = sizeof(T) == 4 ? 3 : 1;   // resident CTAs per SM the registers are sized for
     static bool attr_set = false;   // per instantiation; set before the first launch
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_step<T, TX, TY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);

@@ -41,15 +41,18 @@ struct FusedLayout {
     static constexpr int NR1 = 7 + 18;                       // R1 planes
     static constexpr size_t al(size_t v) { return (v + 15) / 16 * 16; }
     static constexpr size_t o_geo = 0;                       // 11 T arrays + 2 int arrays of NG
-    static constexpr size_t o_un = al(o_geo + (sizeof(T) * 11 + sizeof(int) * 2) * NG);
-    static constexpr size_t un_phi = sizeof(phi_t<T>) * A4;
-    static constexpr size_t un_flux = sizeof(T) * 12 * NFT;
-    static constexpr size_t o_mu = al(o_un + (un_phi > un_flux ? un_phi : un_flux));
+    static constexpr size_t o_phi = al(o_geo + (sizeof(T) * 11 + sizeof(int) * 2) * NG);
+    static constexpr size_t o_mu = al(o_phi + sizeof(phi_t<T>) * A4);
     static constexpr size_t o_p = al(o_mu + sizeof(T) * A3);
     static constexpr size_t o_r1 = al(o_p + sizeof(T) * A2);
-    static constexpr size_t o_f = al(o_r1 + sizeof(T) * NR1 * A1);   // tilde f on R2, [Q][A2]
-    static constexpr size_t o_g = al(o_f + sizeof(T) * Q * A2);      // tilde g on R1, [Q][A1]
-    static constexpr size_t bytes = al(o_g + sizeof(T) * Q * A1);
+    // tilde f on R2 and tilde g on R1 (phases 1-4); the face fluxes (phase
+    // 5-6) reuse the same bytes once the bar-plus phase is done
+    static constexpr size_t o_un = al(o_r1 + sizeof(T) * NR1 * A1);
+    static constexpr size_t un_fg = sizeof(T) * Q * (A2 + A1);
+    static constexpr size_t un_flux = sizeof(T) * 12 * NFT;
+    static constexpr size_t o_f = o_un;
+    static constexpr size_t o_g = o_un + sizeof(T) * Q * A2;
+    static constexpr size_t bytes = al(o_un + (un_fg > un_flux ? un_fg : un_flux));
 };
 
 // Asynchronous global -> shared copies (cp.async), grouped and awaited.
@@ -83,7 +86,7 @@ struct Tile {
     T *ga;          // [11][NG] geometry coefficients, positions x -4..BX+3 then y -4..BY+3
     int *gg, *gf;   // [NG] global index (-1 outside), flags: 1 om=-1, 2 op=+1, 4 lo wall, 8 hi wall
     phi_t<T> *phi;  // R4
-    T *flux;        // [12][NFT], aliases phi (phi is dead once phase 4 ends)
+    T *flux;        // [12][NFT], aliases sf and sg (dead once phase 4 ends)
     T *mu;          // R3
     T *p;           // R2
     T *gmx, *gmy, *lmu, *gfx, *gfy, *gpx, *gpy;  // R1
@@ -95,7 +98,7 @@ struct Tile {
         ga = (T *)(sm + L::o_geo);
         gg = (int *)(ga + 11 * L::NG);
         gf = gg + L::NG;
-        phi = (phi_t<T> *)(sm + L::o_un);
+        phi = (phi_t<T> *)(sm + L::o_phi);
         flux = (T *)(sm + L::o_un);
         mu = (T *)(sm + L::o_mu);
         p = (T *)(sm + L::o_p);
@@ -154,7 +157,7 @@ __device__ __forceinline__ void face_tail(const InstDev &I, const T (&fb)[Q], co
     Pt<T> s;
     s.phi = phi;
     s.rho = rho_of<T>(I, phi);
-    const T irho = T(1) / s.rho;
+    const T irho = fdiv(T(1), s.rho);
     s.Fx = -phi * ax.gmux + (s.rho - Pr.rho_ref) * Pr.gxa;
     s.Fy = -phi * ax.gmuy + (s.rho - Pr.rho_ref) * Pr.gya;
     s.grx = Pr.drho * ax.gphix;
@@ -174,7 +177,7 @@ __device__ __forceinline__ void face_tail(const InstDev &I, const T (&fb)[Q], co
     s.gpy = ax.gpy;
     const T tf = tauf_of<T>(I, phi, s.rho), tg = Pr.tau_g;
     const PtInv<T> v = pt_inv<T>(I, s);
-    const T r1 = T(1) / (T(2) * tf + h), r2 = T(1) / (T(2) * tg + h);
+    const T r1 = fdiv(T(1), T(2) * tf + h), r2 = fdiv(T(1), T(2) * tg + h);
     const T a1 = T(2) * tf * r1, b1 = h * r1, c1 = tf * h * r1;
     const T a2 = T(2) * tg * r2, b2 = h * r2, c2 = tg * h * r2;
     T fo[Q], go[Q];
@@ -438,7 +441,7 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
                 if (cx(q)) mx += T(cx(q)) * v;
                 if (cy(q)) my += T(cy(q)) * v;
             }
-            const T irho = T(1) / rho;
+            const T irho = fdiv(T(1), rho);
             const T ux = (T(3) * mx + hdt * Fx) * irho;
             const T uy = (T(3) * my + hdt * Fy) * irho;
             vp = sf + hdt * cs2 * (ux * Pr.drho * gfx + uy * Pr.drho * gfy - Pr.gamma * rho * Pr.lambda * lmu);
@@ -449,7 +452,7 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
 
     // ---- phase 4: grad p, u and bar-plus of both distributions on R1 (Eq. relations1)
     const T dt = Pr.dt, h = Pr.h, tg = Pr.tau_g;
-    const T rg = T(1) / (T(2) * tg + dt);
+    const T rg = fdiv(T(1), T(2) * tg + dt);
     const T ag = (T(2) * tg - h) * rg, bg = T(3) * h * rg, cg = T(3) * tg * h * rg;
     for (int r = tid; r < L::A1; r += NT) {
         const int x = r % L::W1 - 1, y = r / L::W1 - 1;
@@ -488,7 +491,7 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
         s.rho = rho_of<T>(I, s.phi);
         s.Fx = -s.phi * gmx + (s.rho - Pr.rho_ref) * Pr.gxa;
         s.Fy = -s.phi * gmy + (s.rho - Pr.rho_ref) * Pr.gya;
-        const T irho = T(1) / s.rho;
+        const T irho = fdiv(T(1), s.rho);
         s.ux = (T(3) * mx + hdt * s.Fx) * irho;
         s.uy = (T(3) * my + hdt * s.Fy) * irho;
         s.p = p0;
@@ -499,7 +502,7 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
         s.gpx = gpx;
         s.gpy = gpy;
         const T tf = tauf_of<T>(I, s.phi, s.rho);
-        const T rf = T(1) / (T(2) * tf + dt);
+        const T rf = fdiv(T(1), T(2) * tf + dt);
         const T af = (T(2) * tf - h) * rf, bf = T(3) * h * rf, cf = T(3) * tf * h * rf;
         const PtInv<T> v = pt_inv<T>(I, s);
 #pragma unroll
@@ -543,15 +546,15 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
         }
     }
     const long long c = cell(gi, gj);
-    const int r1 = TL::i1(x, y), r2 = TL::i2(x, y);
+    const int r1 = TL::i1(x, y);
     const T dtv = dt / (S.c(10, 0, x) * S.c(10, 1, y));
     bool finite = true;
     if constexpr (sizeof(T) == sizeof(double)) {
         T phi = 0;
 #pragma unroll
         for (int q = 0; q < Q; q++) {
-            const T fn = T(4.0 / 3.0) * S.bp[q * L::A1 + r1] - T(1.0 / 3.0) * S.sf[q * L::A2 + r2] - dtv * Jf[q];
-            const T gn = T(4.0 / 3.0) * S.bp[(Q + q) * L::A1 + r1] - T(1.0 / 3.0) * S.sg[q * L::A1 + r1] - dtv * Jg[q];
+            const T fn = T(4.0 / 3.0) * S.bp[q * L::A1 + r1] - T(1.0 / 3.0) * io.f_in[q * N + c] - dtv * Jf[q];
+            const T gn = T(4.0 / 3.0) * S.bp[(Q + q) * L::A1 + r1] - T(1.0 / 3.0) * io.g_in[q * N + c] - dtv * Jg[q];
             io.f_out[q * N + c] = fn;
             io.g_out[q * N + c] = gn;
             phi += gn;
@@ -564,12 +567,12 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
         T jsum = 0, gsum = 0;
 #pragma unroll
         for (int q = 0; q < Q; q++) {
-            const T fn = T(4.0 / 3.0) * S.bp[q * L::A1 + r1] - T(1.0 / 3.0) * S.sf[q * L::A2 + r2] - dtv * Jf[q];
+            const T fn = T(4.0 / 3.0) * S.bp[q * L::A1 + r1] - T(1.0 / 3.0) * io.f_in[q * N + c] - dtv * Jf[q];
             io.f_out[q * N + c] = fn;
             finite = finite && isfinite(fn);
             jsum += Jg[q];
             if (q > 0) {
-                const T gn = T(4.0 / 3.0) * S.bp[(Q + q) * L::A1 + r1] - T(1.0 / 3.0) * S.sg[q * L::A1 + r1] - dtv * Jg[q];
+                const T gn = T(4.0 / 3.0) * S.bp[(Q + q) * L::A1 + r1] - T(1.0 / 3.0) * io.g_in[q * N + c] - dtv * Jg[q];
                 io.g_out[q * N + c] = gn;
                 gsum += gn;
                 finite = finite && isfinite(gn);

@@ -20,6 +20,12 @@ struct Cst {
     static constexpr T half = T(0.5);
 };
 
+// a / b: IEEE division in FP64 mode; in FP32 mode the fast reciprocal-based
+// division (within 2 ulp), used only for 1/rho, 1/(2 tau + dt) and the mixed
+// viscosity, all well away from overflow.
+__device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+
 __device__ __forceinline__ long long cell_of(const InstDev &I, int i, int j)
 {
     return I.cell0 + (long long)j * I.nxp + i;
@@ -39,8 +45,8 @@ __device__ __forceinline__ T tauf_of(const InstDev &I, T phi, T rho)
     const ParT<T> &Pr = par<T>(I);
     // Eq. (mixvis) and tau_f = nu / c_s^2 with nu = mu / rho (Eq. kineticandmobility)
     T muA = Pr.muA, muB = Pr.muB;
-    T mu = muA * muB * (Pr.phiA - Pr.phiB) / ((phi - Pr.phiB) * muB + (Pr.phiA - phi) * muA);
-    return mu / (rho * Cst<T>::cs2);
+    T mu = fdiv(muA * muB * (Pr.phiA - Pr.phiB), (phi - Pr.phiB) * muB + (Pr.phiA - phi) * muA);
+    return fdiv(T(3) * mu, rho);
 }
 
 // Point state from which equilibria and sources follow.
@@ -72,7 +78,7 @@ __device__ __forceinline__ PtInv<T> pt_inv(const InstDev &I, const Pt<T> &s)
     v.prho = cs2 * s.rho;
     v.emu = Pr.eta * s.mu;
     v.srcF = cs2 * s.rho * Pr.gamma * Pr.lambda * s.lapmu;
-    v.fg = T(3) * s.phi / s.rho;
+    v.fg = fdiv(T(3) * s.phi, s.rho);
     v.Gx = s.Fx - s.gpx;
     v.Gy = s.Fy - s.gpy;
     v.cgx = cs2 * s.grx;
