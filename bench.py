@@ -35,6 +35,30 @@ from paper_1802_02868_gb300 import inputs as I  # noqa: E402
 METRIC = "cell-updates/s (f+g, D2Q9)"
 UNIT = "cell-updates/s"
 
+# Algorithmic floating-point operations of one cell update (FMA = 2, divide =
+# 1), counted from the formulas of the step: cell macros, equilibria, sources
+# and bar-plus 531; two faces x 723 (reconstruction of 18 bar distributions,
+# face macros, six equilibria/sources/originals per kind, flux); update 150.
+FLOP_PER_CELL_UPDATE = 2127.0
+# ALU peaks from the unit counts and the maximum SM clock: 152 SMs x 128 FP32
+# lanes x 2 flop x 2.07 GHz, and 152 SMs x 2 DFMA/cycle x 2 flop x 2.07 GHz.
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM bytes per cell of one k_step launch from the ncu capture summarised in
+# profiles/k_step_fp32_drop2048.md (dram__bytes_read.sum + dram__bytes_write.sum
+# over 4,194,304 cells), valid only for the kernel sources it was taken on.
+TRAFFIC_SOURCES_SHA = "b369c0a6d3d7c511"
+TRAFFIC_BYTES_PER_CELL_FP32 = (336.804864e6 + 297.830400e6) / 4194304
+
+
+def kernel_sources_sha():
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1802_02868_gb300", "csrc", "*.cuh"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
 
 def workload(name, seed):
     if name == "batch":
@@ -182,7 +206,7 @@ def run_reference(args, cases, desc):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batch", choices=["batch", "rt", "drop", "roofline"])
@@ -276,17 +300,26 @@ def main():
            "d2h_bytes_per_step": d2h,
            "note": "init from pinned host phi + K steps each followed by a conservation read-back + moments to host"}
 
-    # ---- roofline of the dominant kernel
+    # ---- roofline of the dominant kernel: ALU bound (see FLOP_PER_CELL_UPDATE);
+    # the HBM view of the same launch is reported beside it
     best = max(range(dugks.NUM_KERNELS), key=lambda k: ktimes[dugks.kernel_name(k)][0])
     kname = dugks.kernel_name(best)
     kms, kn = ktimes[kname]
     avg_s = kms / max(kn, 1) * 1e-3
     bpc = sim.kernel_bytes_per_cell(best)
-    achieved = bpc * ncells / avg_s / 1e9
-    peak, peak_kind = measured_peak_hbm()
-    roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "peak_source": peak_kind, "traffic": None,
-            "bytes_per_cell": bpc, "avg_launch_ms": avg_s * 1e3,
+    hbm_achieved = bpc * ncells / avg_s / 1e9
+    peak_hbm, peak_kind = measured_peak_hbm()
+    tflops = FLOP_PER_CELL_UPDATE * ncells / avg_s / 1e12
+    peak_alu = PEAK_FP32_TFLOPS if prec == dugks.FP32 else PEAK_FP64_TFLOPS
+    traffic = None
+    if kname == "k_step" and prec == dugks.FP32 and kernel_sources_sha() == TRAFFIC_SOURCES_SHA:
+        traffic = TRAFFIC_BYTES_PER_CELL_FP32 * ncells
+    roof = {"bound": "alu", "kernel": kname, "achieved": tflops, "peak": peak_alu, "unit": "TFLOP/s",
+            "frac": tflops / peak_alu, "peak_source": "unit counts x 2.07 GHz max SM clock (%s)" % (
+                "FP32 FMA lanes" if prec == dugks.FP32 else "FP64 DFMA rate"),
+            "flop_per_cell": FLOP_PER_CELL_UPDATE, "traffic": traffic, "avg_launch_ms": avg_s * 1e3,
+            "hbm": {"achieved": hbm_achieved, "peak": peak_hbm, "unit": "GB/s", "frac": hbm_achieved / peak_hbm,
+                    "peak_source": peak_kind, "algorithmic_bytes_per_cell": bpc},
             "kernel_share": {k: v[0] / max(sum(x[0] for x in ktimes.values()), 1e-12) for k, v in ktimes.items()
                              if v[1]}}
 

@@ -24,6 +24,7 @@ namespace {
 struct EventPair {
     cudaEvent_t a, b;
     int kernel;
+    int count;   // kernel launches between the two events
 };
 
 }  // namespace
@@ -50,6 +51,9 @@ struct dugks_sim {
     void *d_alt = nullptr;        // the state buffer not holding the current state
     double *d_phi_alt = nullptr;
     bool fused = true;            // one-launch step (k_step) or the four-kernel step
+    bool use_graph = true;        // replay multi-step calls from a captured two-step graph
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph2 = nullptr;   // k_step(A -> B), k_step(B -> A)
     int *d_status = nullptr;
     double2 *d_partials = nullptr;
     double2 *d_sums = nullptr;
@@ -166,10 +170,11 @@ cudaEvent_t take_event(dugks_sim *s)
 struct Timed {
     dugks_sim *s;
     int k;
+    int count;
     cudaEvent_t a = nullptr, b = nullptr;
-    Timed(dugks_sim *s_, int k_) : s(s_), k(k_)
+    Timed(dugks_sim *s_, int k_, int count_ = 1) : s(s_), k(k_), count(count_)
     {
-        s->launches++;
+        s->launches += count;
         if (s->timing && k >= 0) {
             a = take_event(s);
             b = take_event(s);
@@ -180,7 +185,7 @@ struct Timed {
     {
         if (a) {
             cudaEventRecord(b, s->stream);
-            s->ev_used.push_back({a, b, k});
+            s->ev_used.push_back({a, b, k, count});
         }
     }
 };
@@ -191,7 +196,7 @@ void harvest_events(dugks_sim *s)
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
             s->k_ms[e.kernel] += ms;
-            s->k_n[e.kernel] += 1;
+            s->k_n[e.kernel] += e.count;
         }
         s->ev_pool.push_back(e.a);
         s->ev_pool.push_back(e.b);
@@ -200,30 +205,118 @@ void harvest_events(dugks_sim *s)
 }
 
 template <typename T>
-int launch_fused(dugks_sim *s)
+constexpr int fused_minb() { return sizeof(T) == 4 ? 3 : 1; }   // resident CTAs per SM the registers are sized for
+
+template <typename T>
+int prepare_fused()
 {
     using L = FusedLayout<T, TX, TY>;
-    constexpr int MINB = sizeof(T) == 4 ? 3 : 1;   // resident CTAs per SM the registers are sized for
     static bool attr_set = false;   // per instantiation; set before the first launch
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_step<T, TX, TY, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+        cudaError_t e = cudaFuncSetAttribute(k_step<T, TX, TY, fused_minb<T>()>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
         if (e != cudaSuccess) return cuda_status(e);
         attr_set = true;
     }
+    return DUGKS_OK;
+}
+
+// the state buffer that does not hold the current state
+template <typename T>
+StepIO<T> step_io(dugks_sim *s)
+{
     Planes<T> &P = planes<T>(s);
-    // the other state buffer: f then g, Q planes each, and its phi plane
     T *alt = (T *)s->d_alt;
     StepIO<T> io;
     io.f_in = P.f; io.g_in = P.g; io.phi_in = P.phi;
     io.f_out = alt; io.g_out = alt + (long long)Q * P.N; io.phi_out = (phi_t<T> *)s->d_phi_alt;
     io.N = P.N;
     io.status = s->d_status;
-    { Timed t(s, K_STEP); k_step<T, TX, TY, MINB><<<(unsigned)s->n_tiles, dim3(TX, TY), L::bytes, s->stream>>>(s->d_inst, s->d_tiles, (const AxisRecT<T> *)s->d_geoT, io); }
-    // swap: the new state becomes current for every other kernel
+    return io;
+}
+
+template <typename T>
+void enqueue_fused(dugks_sim *s, const StepIO<T> &io, cudaStream_t st)
+{
+    using L = FusedLayout<T, TX, TY>;
+    k_step<T, TX, TY, fused_minb<T>()><<<(unsigned)s->n_tiles, dim3(TX, TY), L::bytes, st>>>(
+        s->d_inst, s->d_tiles, (const AxisRecT<T> *)s->d_geoT, io);
+}
+
+// swap: the new state becomes current for every other kernel
+template <typename T>
+void swap_state(dugks_sim *s, const StepIO<T> &io)
+{
+    Planes<T> &P = planes<T>(s);
     s->d_alt = (void *)P.f;
     s->d_phi_alt = (double *)P.phi;
     P.f = io.f_out; P.g = io.g_out; P.phi = io.phi_out;
+}
+
+template <typename T>
+int launch_fused(dugks_sim *s)
+{
+    int rc = prepare_fused<T>();
+    if (rc) return rc;
+    const StepIO<T> io = step_io<T>(s);
+    { Timed t(s, K_STEP); enqueue_fused<T>(s, io, s->stream); }
+    swap_state<T>(s, io);
     return cuda_status(cudaGetLastError());
+}
+
+// Two fused steps captured once into a graph, starting from the state in the
+// first buffer (d_planes); replayed for multi-step calls.
+template <typename T>
+int build_graph2(dugks_sim *s)
+{
+    int rc = prepare_fused<T>();
+    if (rc) return rc;
+    cudaError_t e = cudaSuccess;
+    if (!s->cap_stream) e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_status(e);
+    const StepIO<T> a = step_io<T>(s);   // first buffer -> second
+    StepIO<T> b = a;                     // second -> first
+    b.f_in = a.f_out; b.g_in = a.g_out; b.phi_in = a.phi_out;
+    b.f_out = (T *)a.f_in; b.g_out = (T *)a.g_in; b.phi_out = (phi_t<T> *)a.phi_in;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_status(e);
+    enqueue_fused<T>(s, a, s->cap_stream);
+    enqueue_fused<T>(s, b, s->cap_stream);
+    e = cudaStreamEndCapture(s->cap_stream, &g);
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaGraphInstantiate(&s->graph2, g, 0);
+    cudaGraphDestroy(g);
+    return cuda_status(e);
+}
+
+template <typename T>
+int step_fused(dugks_sim *s, long n)
+{
+    // the graph starts from the first buffer; one plain step realigns
+    const bool in_first = (void *)planes<T>(s).f == s->d_planes;
+    long k = 0;
+    if (n >= 2 && s->use_graph) {
+        if (!in_first) {
+            int rc = launch_fused<T>(s);
+            if (rc) return rc;
+            k++;
+        }
+        if (!s->graph2) {
+            int rc = build_graph2<T>(s);
+            if (rc) return rc;
+        }
+        for (; k + 2 <= n; k += 2) {
+            Timed t(s, K_STEP, 2);
+            cudaError_t e = cudaGraphLaunch(s->graph2, s->stream);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+    }
+    for (; k < n; k++) {
+        int rc = launch_fused<T>(s);
+        if (rc) return rc;
+    }
+    return DUGKS_OK;
 }
 
 template <typename T>
@@ -354,6 +447,8 @@ void free_sim(dugks_sim *s)
     cudaFree(s->d_partials);
     cudaFree(s->d_sums);
     cudaFree(s->d_stage);
+    if (s->graph2) cudaGraphExecDestroy(s->graph2);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     for (auto &e : s->ev_used) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     for (auto e : s->ev_pool) cudaEventDestroy(e);
     delete s;
@@ -395,6 +490,8 @@ int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *para
     {
         const char *env = std::getenv("DUGKS_UNFUSED");
         s->fused = !(env && env[0] == '1');
+        const char *g = std::getenv("DUGKS_NO_GRAPH");
+        s->use_graph = !(g && g[0] == '1');
     }
     s->stream = (cudaStream_t)cuda_stream;
     std::vector<AxisRec> geo;
@@ -547,6 +644,7 @@ int dugks_init(dugks_sim *s, const double *phi, const double *ux, const double *
 int dugks_step(dugks_sim *s, long nsteps)
 {
     if (!s || nsteps < 0) return DUGKS_ERR_ARG;
+    if (s->fused) return s->prec == DUGKS_FP64 ? step_fused<double>(s, nsteps) : step_fused<float>(s, nsteps);
     for (long k = 0; k < nsteps; k++) {
         int rc = s->prec == DUGKS_FP64 ? launch_step<double>(s) : launch_step<float>(s);
         if (rc) return rc;

@@ -170,3 +170,22 @@ def test_fused_step_matches_four_kernel_step(prec, monkeypatch):
     fb, gb = b.state()
     tol = 1e-11 if prec == dugks.FP64 else 2e-5
     assert normwise(fa, fb) < tol and normwise(ga, gb) < tol
+
+
+def test_graph_replay_matches_plain_launches(monkeypatch):
+    """Multi-step calls replay a captured two-step graph; the result is the
+    same bits as stepping with individual launches, from either buffer."""
+    cases = [CASES[0][1], CASES[3][1]]
+    monkeypatch.setenv("DUGKS_NO_GRAPH", "1")
+    a = dugks.Sim([c.mesh for c in cases], [c.params for c in cases], dugks.FP32)
+    monkeypatch.delenv("DUGKS_NO_GRAPH")
+    b = dugks.Sim([c.mesh for c in cases], [c.params for c in cases], dugks.FP32)
+    for s in (a, b):
+        s.init([c.phi0 for c in cases])
+        s.step(1)      # start the multi-step call from the second buffer
+        s.step(7)
+        s.step(4)
+    fa, ga = a.state()
+    fb, gb = b.state()
+    assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+    assert b.launch_count() >= 12
