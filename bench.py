@@ -212,6 +212,7 @@ def main():
     ap.add_argument("--workload", default="batch", choices=["batch", "rt", "drop", "roofline"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -235,6 +236,7 @@ def main():
     # pinned host buffers for the end-to-end leg
     phi_h = torch.from_numpy(np.concatenate([c.phi0.reshape(-1) for c in cases])).pin_memory()
     sim.init(phi_h.numpy())
+    tuned = sim.autotune(steps=3) if not args.no_autotune else (0, dugks.tile_shape_name(0), None)
     for _ in range(args.warmup):
         sim.step(1)
     torch.cuda.synchronize()
@@ -326,7 +328,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32" if prec == dugks.FP32 else "f64", "data": "synthetic",
-            "config": dict(desc, precision=args.precision, l2="inputs larger than L2 (state %.2f GB)" % (
+            "config": dict(desc, precision=args.precision, tile_shape=tuned[1], l2="inputs larger than L2 (state %.2f GB)" % (
                 ncells * 72 * (1 if prec == dugks.FP32 else 2) / 1e9) if ncells * 72 > 129e6 else
                 "inputs smaller than L2: not flushed"),
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk, "instances_finite": n_finite}

@@ -52,6 +52,9 @@ struct dugks_sim {
     double *d_phi_alt = nullptr;
     bool fused = true;            // one-launch step (k_step) or the four-kernel step
     bool use_graph = true;        // replay multi-step calls from a captured two-step graph
+    int shape = 0;                // tile shape of the fused step (index into kShapes)
+    int4 *d_tiles_s[DUGKS_NUM_TILE_SHAPES] = {};
+    int n_tiles_s[DUGKS_NUM_TILE_SHAPES] = {};
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph2 = nullptr;   // k_step(A -> B), k_step(B -> A)
     int *d_status = nullptr;
@@ -69,6 +72,13 @@ struct dugks_sim {
 };
 
 namespace {
+
+// Tile shapes of the fused step that the autotuner chooses from.
+struct ShapeDesc {
+    int bx, by;
+    const char *name;
+};
+const ShapeDesc kShapes[DUGKS_NUM_TILE_SHAPES] = {{32, 8, "32x8"}, {16, 16, "16x16"}, {32, 12, "32x12"}};
 
 const char *kNames[K_COUNT] = {"k_mu", "k_macro", "k_cell", "k_face", "k_init", "k_reduce", "k_step"};
 
@@ -204,21 +214,62 @@ void harvest_events(dugks_sim *s)
     s->ev_used.clear();
 }
 
-template <typename T>
-constexpr int fused_minb() { return sizeof(T) == 4 ? 3 : 1; }   // resident CTAs per SM the registers are sized for
+// Resident CTAs per SM that the registers of a fused-step instantiation are
+// sized for (shared memory allows the same count).
+template <typename T, int BX, int BY>
+constexpr int fused_minb() { return sizeof(T) == 8 ? 1 : (BX * BY > 256 ? 2 : 3); }
 
-template <typename T>
-int prepare_fused()
+template <typename T, int BX, int BY>
+int prepare_shape()
 {
-    using L = FusedLayout<T, TX, TY>;
+    using L = FusedLayout<T, BX, BY>;
     static bool attr_set = false;   // per instantiation; set before the first launch
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_step<T, TX, TY, fused_minb<T>()>,
+        cudaError_t e = cudaFuncSetAttribute(k_step<T, BX, BY, fused_minb<T, BX, BY>()>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
         if (e != cudaSuccess) return cuda_status(e);
         attr_set = true;
     }
     return DUGKS_OK;
+}
+
+// tile table of shape k (shape 0 is the table every other kernel uses)
+int ensure_tiles(dugks_sim *s, int k)
+{
+    if (k == 0) {
+        s->d_tiles_s[0] = s->d_tiles;
+        s->n_tiles_s[0] = s->n_tiles;
+        return DUGKS_OK;
+    }
+    if (s->d_tiles_s[k]) return DUGKS_OK;
+    std::vector<int4> tiles;
+    const int bx = kShapes[k].bx, by = kShapes[k].by;
+    for (int i = 0; i < s->n_inst; i++) {
+        const InstDev &I = s->h_inst[i];
+        for (int ty = 0; ty < I.ny; ty += by)
+            for (int tx = 0; tx < I.nx; tx += bx) tiles.push_back(make_int4(i, tx, ty, 0));
+    }
+    cudaError_t e = cudaMalloc(&s->d_tiles_s[k], sizeof(int4) * tiles.size());
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_tiles_s[k], tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(s->d_tiles_s[k]);
+        s->d_tiles_s[k] = nullptr;
+        return cuda_status(e);
+    }
+    s->n_tiles_s[k] = (int)tiles.size();
+    return DUGKS_OK;
+}
+
+template <typename T>
+int prepare_fused(dugks_sim *s)
+{
+    int rc = ensure_tiles(s, s->shape);
+    if (rc) return rc;
+    switch (s->shape) {
+    case 1: return prepare_shape<T, 16, 16>();
+    case 2: return prepare_shape<T, 32, 12>();
+    default: return prepare_shape<T, 32, 8>();
+    }
 }
 
 // the state buffer that does not hold the current state
@@ -235,12 +286,22 @@ StepIO<T> step_io(dugks_sim *s)
     return io;
 }
 
+template <typename T, int BX, int BY>
+void enqueue_shape(dugks_sim *s, int k, const StepIO<T> &io, cudaStream_t st)
+{
+    using L = FusedLayout<T, BX, BY>;
+    k_step<T, BX, BY, fused_minb<T, BX, BY>()><<<(unsigned)s->n_tiles_s[k], dim3(BX, BY), L::bytes, st>>>(
+        s->d_inst, s->d_tiles_s[k], (const AxisRecT<T> *)s->d_geoT, io);
+}
+
 template <typename T>
 void enqueue_fused(dugks_sim *s, const StepIO<T> &io, cudaStream_t st)
 {
-    using L = FusedLayout<T, TX, TY>;
-    k_step<T, TX, TY, fused_minb<T>()><<<(unsigned)s->n_tiles, dim3(TX, TY), L::bytes, st>>>(
-        s->d_inst, s->d_tiles, (const AxisRecT<T> *)s->d_geoT, io);
+    switch (s->shape) {
+    case 1: enqueue_shape<T, 16, 16>(s, 1, io, st); break;
+    case 2: enqueue_shape<T, 32, 12>(s, 2, io, st); break;
+    default: enqueue_shape<T, 32, 8>(s, 0, io, st); break;
+    }
 }
 
 // swap: the new state becomes current for every other kernel
@@ -256,7 +317,7 @@ void swap_state(dugks_sim *s, const StepIO<T> &io)
 template <typename T>
 int launch_fused(dugks_sim *s)
 {
-    int rc = prepare_fused<T>();
+    int rc = prepare_fused<T>(s);
     if (rc) return rc;
     const StepIO<T> io = step_io<T>(s);
     { Timed t(s, K_STEP); enqueue_fused<T>(s, io, s->stream); }
@@ -269,7 +330,7 @@ int launch_fused(dugks_sim *s)
 template <typename T>
 int build_graph2(dugks_sim *s)
 {
-    int rc = prepare_fused<T>();
+    int rc = prepare_fused<T>(s);
     if (rc) return rc;
     cudaError_t e = cudaSuccess;
     if (!s->cap_stream) e = cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking);
@@ -436,6 +497,7 @@ void free_sim(dugks_sim *s)
     if (!s) return;
     cudaFree(s->d_inst);
     cudaFree(s->d_tiles);
+    for (int k = 1; k < DUGKS_NUM_TILE_SHAPES; k++) cudaFree(s->d_tiles_s[k]);
     cudaFree(s->d_geo);
     cudaFree(s->d_geoT);
     cudaFree(s->d_dense0);
@@ -796,6 +858,105 @@ int dugks_kernel_bytes_per_cell(const dugks_sim *s, int k, double *bytes)
     }
     *bytes = b;
     return DUGKS_OK;
+}
+
+int dugks_set_tile_shape(dugks_sim *s, int shape)
+{
+    if (!s || shape < 0 || shape >= DUGKS_NUM_TILE_SHAPES) return DUGKS_ERR_ARG;
+    if (!s->fused) return shape == 0 ? DUGKS_OK : DUGKS_ERR_UNSUPPORTED;
+    if (shape != s->shape) {
+        cudaError_t e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return cuda_status(e);
+        if (s->graph2) {
+            cudaGraphExecDestroy(s->graph2);
+            s->graph2 = nullptr;
+        }
+        s->shape = shape;
+    }
+    return s->prec == DUGKS_FP64 ? prepare_fused<double>(s) : prepare_fused<float>(s);
+}
+
+int dugks_tile_shape(const dugks_sim *s, int *shape, int *bx, int *by)
+{
+    if (!s) return DUGKS_ERR_ARG;
+    if (shape) *shape = s->shape;
+    if (bx) *bx = kShapes[s->shape].bx;
+    if (by) *by = kShapes[s->shape].by;
+    return DUGKS_OK;
+}
+
+int dugks_autotune(dugks_sim *s, int steps, int *chosen, double *ms_per_step)
+{
+    if (!s || steps < 1) return DUGKS_ERR_ARG;
+    if (!s->fused) {
+        if (chosen) *chosen = 0;
+        return DUGKS_OK;
+    }
+    const bool f64 = s->prec == DUGKS_FP64;
+    const size_t esz = f64 ? sizeof(double) : sizeof(float);
+    const size_t fg_bytes = esz * 2 * Q * (size_t)s->N, phi_bytes = sizeof(double) * (size_t)s->N;
+    const size_t st_bytes = sizeof(int) * s->n_inst;
+    // snapshot of the current state, restored after every trial
+    void *snap = nullptr;
+    cudaError_t e = cudaMalloc(&snap, fg_bytes + phi_bytes + st_bytes);
+    if (e != cudaSuccess) return cuda_status(e);
+    auto cur = [&](void **fg, void **phi) {
+        if (f64) { *fg = s->P64.f; *phi = s->P64.phi; }
+        else { *fg = s->P32.f; *phi = s->P32.phi; }
+    };
+    void *fg, *phi;
+    cur(&fg, &phi);
+    e = cudaMemcpyAsync(snap, fg, fg_bytes, cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync((char *)snap + fg_bytes, phi, phi_bytes, cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync((char *)snap + fg_bytes + phi_bytes, s->d_status, st_bytes, cudaMemcpyDeviceToDevice, s->stream);
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    const bool timing = s->timing;
+    s->timing = false;
+    const long launches = s->launches;
+    int best = 0, rc = DUGKS_OK;
+    float best_ms = 0.f;
+    for (int k = 0; k < DUGKS_NUM_TILE_SHAPES && e == cudaSuccess && rc == DUGKS_OK; k++) {
+        rc = dugks_set_tile_shape(s, k);
+        if (rc) break;
+        rc = dugks_step(s, 1);   // warm-up (first launch of the instantiation)
+        if (rc) break;
+        e = cudaEventRecord(a, s->stream);
+        if (e != cudaSuccess) break;
+        rc = dugks_step(s, steps);
+        if (rc) break;
+        e = cudaEventRecord(b, s->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e != cudaSuccess) break;
+        if (k == 0 || ms < best_ms) { best = k; best_ms = ms; }
+        // restore the state into whichever buffers are current now
+        cur(&fg, &phi);
+        e = cudaMemcpyAsync(fg, snap, fg_bytes, cudaMemcpyDeviceToDevice, s->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(phi, (char *)snap + fg_bytes, phi_bytes, cudaMemcpyDeviceToDevice, s->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_status, (char *)snap + fg_bytes + phi_bytes, st_bytes, cudaMemcpyDeviceToDevice, s->stream);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFree(snap);
+    s->timing = timing;
+    s->launches = launches;
+    if (rc == DUGKS_OK && e != cudaSuccess) rc = cuda_status(e);
+    if (rc == DUGKS_OK) rc = dugks_set_tile_shape(s, best);
+    if (rc == DUGKS_OK) {
+        if (chosen) *chosen = best;
+        if (ms_per_step) *ms_per_step = best_ms / steps;
+    }
+    return rc;
+}
+
+const char *dugks_tile_shape_name(int shape)
+{
+    if (shape < 0 || shape >= DUGKS_NUM_TILE_SHAPES) return "?";
+    return kShapes[shape].name;
 }
 
 const char *dugks_status_str(int st)

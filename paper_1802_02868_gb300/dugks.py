@@ -51,7 +51,8 @@ _lib = None
 EXPORTS = ("dugks_create", "dugks_batch_create", "dugks_destroy", "dugks_init", "dugks_step", "dugks_moments",
            "dugks_conservation", "dugks_batch_status", "dugks_dt", "dugks_info", "dugks_save", "dugks_load",
            "dugks_launch_count", "dugks_set_timing", "dugks_kernel_times", "dugks_kernel_name",
-           "dugks_kernel_bytes_per_cell", "dugks_status_str", "dugks_conservation_static")
+           "dugks_kernel_bytes_per_cell", "dugks_status_str", "dugks_conservation_static",
+           "dugks_autotune", "dugks_set_tile_shape", "dugks_tile_shape", "dugks_tile_shape_name")
 STATIC_MAX_CELLS = 16777216
 
 
@@ -91,10 +92,15 @@ def load(build_if_missing: bool = True):
     L.dugks_kernel_name.restype = ctypes.c_char_p
     L.dugks_kernel_bytes_per_cell.argtypes = [vp, ip, dp]
     L.dugks_conservation_static.argtypes = [vp, vp, vp, ip, ip] + [ctypes.c_double] * 4 + [vp, vp]
+    L.dugks_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), dp]
+    L.dugks_set_tile_shape.argtypes = [vp, ip]
+    L.dugks_tile_shape.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int)] * 3
+    L.dugks_tile_shape_name.argtypes = [ip]
+    L.dugks_tile_shape_name.restype = ctypes.c_char_p
     L.dugks_status_str.argtypes = [ip]
     L.dugks_status_str.restype = ctypes.c_char_p
     for n in EXPORTS:
-        if n not in ("dugks_destroy", "dugks_kernel_name", "dugks_status_str"):
+        if n not in ("dugks_destroy", "dugks_kernel_name", "dugks_status_str", "dugks_tile_shape_name"):
             getattr(L, n).restype = ctypes.c_int
     _lib = L
     return L
@@ -249,6 +255,22 @@ class Sim:
         _check("dugks_kernel_times", load().dugks_kernel_times(self.h, _dp(ms), n))
         return {kernel_name(k): (ms[k], n[k]) for k in range(NUM_KERNELS)}
 
+    def autotune(self, steps=5):
+        """Time every tile shape of the fused step on the current state (which is
+        restored) and keep the fastest; returns (shape index, name, ms per step)."""
+        k = ctypes.c_int()
+        ms = ctypes.c_double()
+        _check("dugks_autotune", load().dugks_autotune(self.h, int(steps), ctypes.byref(k), ctypes.byref(ms)))
+        return k.value, tile_shape_name(k.value), ms.value
+
+    def set_tile_shape(self, shape):
+        _check("dugks_set_tile_shape", load().dugks_set_tile_shape(self.h, int(shape)))
+
+    def tile_shape(self):
+        k, bx, by = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check("dugks_tile_shape", load().dugks_tile_shape(self.h, ctypes.byref(k), ctypes.byref(bx), ctypes.byref(by)))
+        return k.value, bx.value, by.value
+
     def kernel_bytes_per_cell(self, k):
         v = ctypes.c_double()
         _check("dugks_kernel_bytes_per_cell", load().dugks_kernel_bytes_per_cell(self.h, int(k), ctypes.byref(v)))
@@ -263,6 +285,13 @@ def conservation_static(phi_ptr, dx_ptr, dy_ptr, nx, ny, params, out_ptr, stream
                                             ctypes.c_void_p(int(dy_ptr)), int(nx), int(ny), params.phiA,
                                             params.phiB, params.rhoA, params.rhoB, ctypes.c_void_p(int(out_ptr)),
                                             ctypes.c_void_p(int(stream)))
+
+
+NUM_TILE_SHAPES = 3
+
+
+def tile_shape_name(k):
+    return load().dugks_tile_shape_name(int(k)).decode()
 
 
 def kernel_name(k):

@@ -189,3 +189,33 @@ def test_graph_replay_matches_plain_launches(monkeypatch):
     fb, gb = b.state()
     assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
     assert b.launch_count() >= 12
+
+
+@pytest.mark.parametrize("prec", [dugks.FP64, dugks.FP32])
+def test_tile_shapes_agree_and_autotune_restores_state(prec):
+    """Every tile shape of the fused step computes the same scheme; the autotuner
+    leaves the state as it found it and keeps one of the shapes."""
+    cases = [CASES[0][1], CASES[3][1], CASES[5][1], CASES[7][1]]
+    sims = []
+    for k in range(dugks.NUM_TILE_SHAPES):
+        s = dugks.Sim([c.mesh for c in cases], [c.params for c in cases], prec)
+        s.set_tile_shape(k)
+        s.init([c.phi0 for c in cases])
+        s.step(13)
+        sims.append(s)
+    f0, g0 = sims[0].state()
+    tol = 1e-13 if prec == dugks.FP64 else 1e-6
+    for s in sims[1:]:
+        f, g = s.state()
+        assert normwise(f, f0) < tol and normwise(g, g0) < tol
+    s = sims[0]
+    before = s.state()
+    k, name, ms = s.autotune(steps=3)
+    after = s.state()
+    assert 0 <= k < dugks.NUM_TILE_SHAPES and ms > 0 and s.tile_shape()[0] == k
+    assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+    s.step(2)
+    sims[1].step(2)
+    f, g = s.state()
+    f1, g1 = sims[1].state()
+    assert normwise(f, f1) < tol and normwise(g, g1) < tol
