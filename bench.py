@@ -173,6 +173,29 @@ def cpu_baseline(cases, precision_name, budget_s=12.0):
                 len(sample), len(cases), cells, steps, dt)}
 
 
+def fp64_single_instance_rate(dugks, torch, cases, n_sample=16, steps=3):
+    """Cell-updates/s of the plain path: instances stepped one at a time as
+    single-instance FP64 simulations (a seeded sample of the workload)."""
+    rng = np.random.default_rng(7)
+    idx = sorted(rng.choice(len(cases), size=min(n_sample, len(cases)), replace=False).tolist())
+    total_ms, cell_updates = 0.0, 0
+    stream = torch.cuda.current_stream()
+    for k in idx:
+        c = cases[k]
+        s = dugks.Sim(c.mesh, c.params, dugks.FP64, stream=stream.cuda_stream).init(c.phi0)
+        s.step(1)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            s.step(1)
+        b.record(stream)
+        b.synchronize()
+        total_ms += a.elapsed_time(b)
+        cell_updates += steps * c.mesh.ncells
+        s.close()
+    return cell_updates / (total_ms * 1e-3), len(idx)
+
+
 def run_reference(args, cases, desc):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -332,6 +355,11 @@ def main():
                 ncells * 72 * (1 if prec == dugks.FP32 else 2) / 1e9) if ncells * 72 > 129e6 else
                 "inputs smaller than L2: not flushed"),
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk, "instances_finite": n_finite}
+    if rank == 0 and ws == 1 and len(cases) > 1 and prec == dugks.FP32:
+        rate64, nsamp = fp64_single_instance_rate(dugks, torch, cases)
+        line["speedup_vs_fp64_single_instance"] = {
+            "fp64_single_instance_value": rate64, "unit": UNIT, "ratio": (value / ws) / rate64,
+            "sample": "%d instances, each its own FP64 simulation, stepped one at a time" % nsamp}
     if rank == 0 and not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_baseline(cases, args.precision)
     if rank == 0:

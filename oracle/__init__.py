@@ -21,24 +21,36 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "dugks_oracle.c")
 BUILD_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD_DIR, "liboracle.so")
+LIB_CS = os.path.join(BUILD_DIR, "liboracle_cs.so")   # double complex build (complex step)
 
 Q = 9
 _lib = None
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle shared library (idempotent)."""
-    os.makedirs(BUILD_DIR, exist_ok=True)
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
-        return LIB
-    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", SRC]
-    tmp = LIB + ".tmp.%d" % os.getpid()
+def _compile(out, defines=()):
+    if os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(SRC):
+        return out
+    base = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off"] + list(defines) + [SRC]
+    tmp = out + ".tmp.%d" % os.getpid()
     try:
         subprocess.run(base + ["-fopenmp", "-o", tmp, "-lm"], check=True,
                        stdout=subprocess.PIPE, stderr=subprocess.PIPE)
     except subprocess.CalledProcessError:
         subprocess.run(base + ["-o", tmp, "-lm"], check=True)
-    os.replace(tmp, LIB)
+    os.replace(tmp, out)
+    return out
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared libraries (idempotent): the double build and
+    the double-complex build used for complex-step derivatives."""
+    os.makedirs(BUILD_DIR, exist_ok=True)
+    if force:
+        for f in (LIB, LIB_CS):
+            if os.path.exists(f):
+                os.remove(f)
+    _compile(LIB)
+    _compile(LIB_CS, ["-DORACLE_COMPLEX"])
     return LIB
 
 
@@ -232,6 +244,102 @@ class Oracle:
         gb = np.zeros((Q, self.ny, self.nx))
         lib().oracle_bar_plus_fields(self.h, _p(fb), _p(gb))
         return fb, gb
+
+
+_lib_cs = None
+
+
+def lib_cs():
+    global _lib_cs
+    if _lib_cs is None:
+        build()
+        L = ctypes.CDLL(LIB_CS)
+        dp = ctypes.POINTER(ctypes.c_double)
+        vp = ctypes.c_void_p
+        L.oracle_create.restype = vp
+        L.oracle_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, dp, dp, dp]
+        L.oracle_destroy.argtypes = [vp]
+        L.oracle_init.argtypes = [vp, dp, dp, dp, dp]
+        L.oracle_init.restype = ctypes.c_int
+        L.oracle_step.argtypes = [vp, ctypes.c_long]
+        L.oracle_step.restype = ctypes.c_int
+        L.oracle_moments.argtypes = [vp, dp, dp, dp, dp, dp]
+        L.oracle_get_state.argtypes = [vp, dp, dp]
+        _lib_cs = L
+    return _lib_cs
+
+
+def _cp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+class OracleCS:
+    """The oracle in double complex arithmetic, for complex-step derivatives.
+    ``params`` is a list of 14 complex numbers in the order of
+    ``Params.as_list()`` (the CFL number's real part is used)."""
+
+    def __init__(self, mesh, params_complex):
+        L = lib_cs()
+        self.nx, self.ny = int(mesh.dx.size), int(mesh.dy.size)
+        self.N = self.nx * self.ny
+        self._dx = _c(mesh.dx)
+        self._dy = _c(mesh.dy)
+        self._prm = np.ascontiguousarray(np.asarray(params_complex, dtype=np.complex128).reshape(14))
+        self.h = L.oracle_create(self.nx, self.ny, int(mesh.bc_x), int(mesh.bc_y), _p(self._dx), _p(self._dy),
+                                 _cp(self._prm))
+        if not self.h:
+            raise ValueError("oracle_create failed")
+
+    def close(self):
+        if self.h:
+            lib_cs().oracle_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, phi):
+        self._phi = np.ascontiguousarray(np.asarray(phi, dtype=np.complex128).reshape(-1))
+        if lib_cs().oracle_init(self.h, _cp(self._phi), None, None, None) != 0:
+            raise FloatingPointError("oracle_init: non-finite state")
+        return self
+
+    def step(self, n=1):
+        if lib_cs().oracle_step(self.h, int(n)) != 0:
+            raise FloatingPointError("oracle_step: non-finite state")
+        return self
+
+    def phi(self):
+        out = np.zeros(self.N, dtype=np.complex128)
+        lib_cs().oracle_moments(self.h, _cp(out), None, None, None, None)
+        return out.reshape(self.ny, self.nx)
+
+
+def complex_step_gradient(mesh, params, phi0, steps, phi_target, direction_phi0=None, which=(), eps=1e-30):
+    """Derivatives of L = sum_cells (phi_T - phi_target)^2 by the complex step:
+    for each parameter name in ``which`` (``"kappa"`` or ``"mobility"``) dL/dparam,
+    and, if ``direction_phi0`` is given, the directional derivative dL/dphi0 . v."""
+    names = ("phiA", "phiB", "rhoA", "rhoB", "nuA", "nuB", "mobility", "tau_g", "beta", "kappa", "gx", "gy",
+             "rho_ref", "cfl")
+    base = np.asarray(params.as_list(), dtype=np.complex128)
+    out = {}
+
+    def loss(prm, phi):
+        o = OracleCS(mesh, prm).init(phi).step(steps)
+        d = o.phi() - phi_target
+        return np.sum(d * d)
+
+    for w in which:
+        prm = base.copy()
+        prm[names.index(w)] += 1j * eps
+        out[w] = loss(prm, np.asarray(phi0, dtype=np.complex128)).imag / eps
+    if direction_phi0 is not None:
+        phi = np.asarray(phi0, dtype=np.complex128) + 1j * eps * np.asarray(direction_phi0)
+        out["phi0_dir"] = loss(base, phi).imag / eps
+    return out
 
 
 def run_case(case, steps=None):

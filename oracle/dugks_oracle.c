@@ -34,6 +34,22 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* The arithmetic type.  The default build is plain double.  Built with
+ * -DORACLE_COMPLEX the same code runs in double complex arithmetic, which
+ * gives exact first derivatives by the complex step: perturb an input by
+ * i*eps (eps ~ 1e-30) and read d(output)/d(input) = Im(output)/eps, free of
+ * subtractive cancellation.  Mesh geometry stays real in both builds. */
+#ifdef ORACLE_COMPLEX
+#include <complex.h>
+typedef double complex real;
+#define FINITE(x) (isfinite(creal(x)) && isfinite(cimag(x)))
+#define creal_or_same(x) creal(x)
+#else
+typedef double real;
+#define FINITE(x) isfinite(x)
+#define creal_or_same(x) (x)
+#endif
+
 #define Q 9
 #define BC_PERIODIC 0
 #define BC_WALL 1
@@ -56,17 +72,19 @@ typedef struct {
     int bc[2];
     double *d[2];    /* cell widths along x (nx) and y (ny) */
     /* parameters */
-    double phiA, phiB, rhoA, rhoB, nuA, nuB, lambda, tau_g, beta, kappa, gx, gy, rho_ref, cfl;
+    real phiA, phiB, rhoA, rhoB, nuA, nuB, lambda, tau_g, beta, kappa, gx, gy, rho_ref;
+    double cfl;
     /* derived */
-    double dt, h, eta, gamma, muA, muB;
+    double dt, h;
+    real eta, gamma, muA, muB;
     /* tracked state: tilde distributions */
-    double *f, *g;
+    real *f, *g;
     /* per-cell macroscopic fields at t_n */
-    double *phi, *rho, *lap_phi, *mu, *lap_mu, *gphi[2], *gmu[2], *F[2], *u[2], *p, *gp[2], *tauf;
+    real *phi, *rho, *lap_phi, *mu, *lap_mu, *gphi[2], *gmu[2], *F[2], *u[2], *p, *gp[2], *tauf;
     /* per-cell bar-plus and tilde-plus distributions (step 2) */
-    double *fbp, *gbp, *ftp, *gtp;
+    real *fbp, *gbp, *ftp, *gtp;
     /* flux accumulators J (Eq. microfluxf) */
-    double *Jf, *Jg;
+    real *Jf, *Jg;
 } osim;
 
 static inline int IDX(const osim *s, int i, int j) { return j * s->nx + i; }
@@ -76,76 +94,76 @@ static inline int IDX(const osim *s, int i, int j) { return j * s->nx + i; }
 /* ------------------------------------------------------------------------- */
 
 /* Eq. (oderrho): density linear in phi */
-static double rho_of(const osim *s, double phi)
+static real rho_of(const osim *s, real phi)
 {
     return (phi - s->phiB) / (s->phiA - s->phiB) * s->rhoA + (s->phiA - phi) / (s->phiA - s->phiB) * s->rhoB;
 }
 
 /* Eq. (mixvis) mixed dynamic viscosity, then nu = mu/rho and tau_f = nu/c_s^2
    (Eq. kineticandmobility) */
-static double tauf_of(const osim *s, double phi, double rho)
+static real tauf_of(const osim *s, real phi, real rho)
 {
-    double mu = s->muA * s->muB * (s->phiA - s->phiB) / ((phi - s->phiB) * s->muB + (s->phiA - phi) * s->muA);
-    double nu = mu / rho;
+    real mu = s->muA * s->muB * (s->phiA - s->phiB) / ((phi - s->phiB) * s->muB + (s->phiA - phi) * s->muA);
+    real nu = mu / rho;
     return nu / CS2;
 }
 
 /* Eq. (chemicalpotential), bulk part psi'(phi) */
-static double dpsi(const osim *s, double phi)
+static real dpsi(const osim *s, real phi)
 {
     return 4.0 * s->beta * (phi - s->phiA) * (phi - s->phiB) * (phi - 0.5 * (s->phiA + s->phiB));
 }
 
 /* Eq. (su) */
-static double s_i(int i, double ux, double uy)
+static real s_i(int i, real ux, real uy)
 {
-    double xu = XI[i][0] * ux + XI[i][1] * uy;
-    double uu = ux * ux + uy * uy;
+    real xu = XI[i][0] * ux + XI[i][1] * uy;
+    real uu = ux * ux + uy * uy;
     return WT[i] * (xu / CS2 + xu * xu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2));
 }
 
 /* Eq. (feq): f_i^eq = omega_i p + c_s^2 rho s_i(u) */
-void oracle_feq(double p, double rho, double ux, double uy, double *out)
+void oracle_feq(real p, real rho, real ux, real uy, real *out)
 {
     for (int i = 0; i < Q; i++) out[i] = WT[i] * p + CS2 * rho * s_i(i, ux, uy);
 }
 
 /* Eqs. (geq), (Hi): g_i^eq = H_i + phi s_i(u) */
-void oracle_geq(double phi, double mu, double eta, double ux, double uy, double *out)
+void oracle_geq(real phi, real mu, real eta, real ux, real uy, real *out)
 {
     for (int i = 0; i < Q; i++) {
-        double H = (i == 0) ? phi - (1.0 - WT[0]) * eta * mu : WT[i] * eta * mu;
+        real H = (i == 0) ? phi - (1.0 - WT[0]) * eta * mu : WT[i] * eta * mu;
         out[i] = H + phi * s_i(i, ux, uy);
     }
 }
 
 /* Eq. (F): F_i^f = (xi_i - u).[F Gamma_i + s_i c_s^2 grad rho] - omega_i c_s^2 rho gamma div(lambda grad mu),
    with Gamma_i = omega_i + s_i and div(lambda grad mu) = lambda lap(mu) (constant lambda) */
-void oracle_src_f(double ux, double uy, double Fx, double Fy, double grx, double gry, double rho,
-                  double gamma, double lambda, double lap_mu, double *out)
+void oracle_src_f(real ux, real uy, real Fx, real Fy, real grx, real gry, real rho,
+                  real gamma, real lambda, real lap_mu, real *out)
 {
     for (int i = 0; i < Q; i++) {
-        double si = s_i(i, ux, uy);
-        double Gi = WT[i] + si;
-        double cx = XI[i][0] - ux, cy = XI[i][1] - uy;
+        real si = s_i(i, ux, uy);
+        real Gi = WT[i] + si;
+        real cx = XI[i][0] - ux, cy = XI[i][1] - uy;
         out[i] = cx * (Fx * Gi + si * CS2 * grx) + cy * (Fy * Gi + si * CS2 * gry)
                - WT[i] * CS2 * rho * gamma * lambda * lap_mu;
     }
 }
 
 /* Eq. (G): F_i^g = phi/(c_s^2 rho) (xi_i - u).(F - grad p) Gamma_i */
-void oracle_src_g(double phi, double rho, double ux, double uy, double Fx, double Fy, double gpx,
-                  double gpy, double *out)
+void oracle_src_g(real phi, real rho, real ux, real uy, real Fx, real Fy, real gpx,
+                  real gpy, real *out)
 {
     for (int i = 0; i < Q; i++) {
-        double Gi = WT[i] + s_i(i, ux, uy);
-        double cx = XI[i][0] - ux, cy = XI[i][1] - uy;
+        real Gi = WT[i] + s_i(i, ux, uy);
+        real cx = XI[i][0] - ux, cy = XI[i][1] - uy;
         out[i] = phi / (CS2 * rho) * (cx * (Fx - gpx) + cy * (Fy - gpy)) * Gi;
     }
 }
 
 /* Eq. (relations1): cell-centre bar-plus from the tilde distribution */
-double oracle_bar_plus(double tilde, double eq, double src, double tau, double dt)
+real oracle_bar_plus(real tilde, real eq, real src, real tau, double dt)
 {
     double h = 0.5 * dt;
     return (2.0 * tau - h) / (2.0 * tau + dt) * tilde + 3.0 * h / (2.0 * tau + dt) * eq
@@ -153,13 +171,13 @@ double oracle_bar_plus(double tilde, double eq, double src, double tau, double d
 }
 
 /* Eq. (relations2) */
-double oracle_tilde_plus(double bar_plus, double tilde)
+real oracle_tilde_plus(real bar_plus, real tilde)
 {
     return 4.0 / 3.0 * bar_plus - 1.0 / 3.0 * tilde;
 }
 
 /* Eq. (original-function): original distribution from the bar one at t+h */
-double oracle_original(double bar, double eq, double src, double tau, double h)
+real oracle_original(real bar, real eq, real src, real tau, double h)
 {
     return 2.0 * tau / (2.0 * tau + h) * bar + h / (2.0 * tau + h) * eq + tau * h / (2.0 * tau + h) * src;
 }
@@ -194,14 +212,14 @@ static int neighbour(const osim *s, int a, int k, int side, int *kn, double *dis
 }
 
 /* value of field Fd at the cell reached from (i,j) by moving to index k on axis a */
-static double at(const osim *s, const double *Fd, int a, int i, int j, int k)
+static real at(const osim *s, const real *Fd, int a, int i, int j, int k)
 {
     return a == 0 ? Fd[IDX(s, k, j)] : Fd[IDX(s, i, k)];
 }
 
 /* Eq. (nonphi): first derivative along axis a with theta_l, theta_r, a, b, c;
    delta is the mean of the two step lengths (any delta gives the same value) */
-static double nonphi(double Fm, double F0, double Fp, double dl, double dr)
+static real nonphi(real Fm, real F0, real Fp, double dl, double dr)
 {
     double delta = 0.5 * (dl + dr);
     double tl = dl / delta, tr = dr / delta;
@@ -210,7 +228,7 @@ static double nonphi(double Fm, double F0, double Fp, double dl, double dr)
 }
 
 /* Eq. (nonphi2): second derivative along axis a */
-static double nonphi2(double Fm, double F0, double Fp, double dl, double dr)
+static real nonphi2(real Fm, real F0, real Fp, double dl, double dr)
 {
     double delta = 0.5 * (dl + dr);
     double tl = dl / delta, tr = dr / delta;
@@ -219,7 +237,7 @@ static double nonphi2(double Fm, double F0, double Fp, double dl, double dr)
 }
 
 /* derivative of a macroscopic cell field along axis a, mirror ghosts at walls */
-static double d1_field(const osim *s, const double *Fd, int a, int i, int j)
+static real d1_field(const osim *s, const real *Fd, int a, int i, int j)
 {
     int k = a == 0 ? i : j, km, kp;
     double dl, dr;
@@ -228,7 +246,7 @@ static double d1_field(const osim *s, const double *Fd, int a, int i, int j)
     return nonphi(at(s, Fd, a, i, j, km), Fd[IDX(s, i, j)], at(s, Fd, a, i, j, kp), dl, dr);
 }
 
-static double d2_field(const osim *s, const double *Fd, int a, int i, int j)
+static real d2_field(const osim *s, const real *Fd, int a, int i, int j)
 {
     int k = a == 0 ? i : j, km, kp;
     double dl, dr;
@@ -239,13 +257,13 @@ static double d2_field(const osim *s, const double *Fd, int a, int i, int j)
 
 /* derivative of a distribution plane along axis a: Eq. (nonphi) between real
    cells; one-sided two-point difference next to a wall */
-static double d1_dist(const osim *s, const double *Fd, int a, int i, int j)
+static real d1_dist(const osim *s, const real *Fd, int a, int i, int j)
 {
     int k = a == 0 ? i : j, km, kp;
     double dl, dr;
     int hasm = neighbour(s, a, k, -1, &km, &dl);
     int hasp = neighbour(s, a, k, +1, &kp, &dr);
-    double F0 = Fd[IDX(s, i, j)];
+    real F0 = Fd[IDX(s, i, j)];
     if (hasm && hasp) return nonphi(at(s, Fd, a, i, j, km), F0, at(s, Fd, a, i, j, kp), dl, dr);
     if (hasp) return (at(s, Fd, a, i, j, kp) - F0) / dr;
     if (hasm) return (F0 - at(s, Fd, a, i, j, km)) / dl;
@@ -259,10 +277,10 @@ static double d1_dist(const osim *s, const double *Fd, int a, int i, int j)
 static void cell_macros(osim *s)
 {
     int nx = s->nx, ny = s->ny, N = nx * ny;
-    double drho = (s->rhoA - s->rhoB) / (s->phiA - s->phiB);
+    real drho = (s->rhoA - s->rhoB) / (s->phiA - s->phiB);
     /* Eq. (phi), Eq. (oderrho) */
     for (int c = 0; c < N; c++) {
-        double phi = 0.0;
+        real phi = 0.0;
         for (int i = 0; i < Q; i++) phi += s->g[i * N + c];
         s->phi[c] = phi;
         s->rho[c] = rho_of(s, phi);
@@ -280,23 +298,23 @@ static void cell_macros(osim *s)
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
             int c = IDX(s, i, j);
-            double gmx = d1_field(s, s->mu, 0, i, j), gmy = d1_field(s, s->mu, 1, i, j);
-            double lmu = d2_field(s, s->mu, 0, i, j) + d2_field(s, s->mu, 1, i, j);
-            double gfx = d1_field(s, s->phi, 0, i, j), gfy = d1_field(s, s->phi, 1, i, j);
-            double phi = s->phi[c], rho = s->rho[c];
-            double Fx = -phi * gmx + (rho - s->rho_ref) * s->gx;
-            double Fy = -phi * gmy + (rho - s->rho_ref) * s->gy;
-            double sf = 0.0, mx = 0.0, my = 0.0;
+            real gmx = d1_field(s, s->mu, 0, i, j), gmy = d1_field(s, s->mu, 1, i, j);
+            real lmu = d2_field(s, s->mu, 0, i, j) + d2_field(s, s->mu, 1, i, j);
+            real gfx = d1_field(s, s->phi, 0, i, j), gfy = d1_field(s, s->phi, 1, i, j);
+            real phi = s->phi[c], rho = s->rho[c];
+            real Fx = -phi * gmx + (rho - s->rho_ref) * s->gx;
+            real Fy = -phi * gmy + (rho - s->rho_ref) * s->gy;
+            real sf = 0.0, mx = 0.0, my = 0.0;
             for (int q = 0; q < Q; q++) {
-                double fq = s->f[q * N + c];
+                real fq = s->f[q * N + c];
                 sf += fq;
                 mx += XI[q][0] * fq;
                 my += XI[q][1] * fq;
             }
-            double ux = (mx + 0.5 * s->dt * CS2 * Fx) / (CS2 * rho);
-            double uy = (my + 0.5 * s->dt * CS2 * Fy) / (CS2 * rho);
-            double grx = drho * gfx, gry = drho * gfy;
-            double p = sf + 0.5 * s->dt * CS2 * (ux * grx + uy * gry - s->gamma * rho * s->lambda * lmu);
+            real ux = (mx + 0.5 * s->dt * CS2 * Fx) / (CS2 * rho);
+            real uy = (my + 0.5 * s->dt * CS2 * Fy) / (CS2 * rho);
+            real grx = drho * gfx, gry = drho * gfy;
+            real p = sf + 0.5 * s->dt * CS2 * (ux * grx + uy * gry - s->gamma * rho * s->lambda * lmu);
             s->gmu[0][c] = gmx; s->gmu[1][c] = gmy; s->lap_mu[c] = lmu;
             s->gphi[0][c] = gfx; s->gphi[1][c] = gfy;
             s->F[0][c] = Fx; s->F[1][c] = Fy;
@@ -315,11 +333,11 @@ static void cell_macros(osim *s)
 
 /* equilibria and sources of both distributions at a point */
 typedef struct {
-    double phi, rho, ux, uy, p, mu, lap_mu, Fx, Fy, grx, gry, gpx, gpy, tauf;
+    real phi, rho, ux, uy, p, mu, lap_mu, Fx, Fy, grx, gry, gpx, gpy, tauf;
 } point_state;
 
-static void point_eq_src(const osim *s, const point_state *ps, double *feq, double *geq, double *Ff,
-                         double *Fg)
+static void point_eq_src(const osim *s, const point_state *ps, real *feq, real *geq, real *Ff,
+                         real *Fg)
 {
     oracle_feq(ps->p, ps->rho, ps->ux, ps->uy, feq);
     oracle_geq(ps->phi, ps->mu, s->eta, ps->ux, ps->uy, geq);
@@ -329,7 +347,7 @@ static void point_eq_src(const osim *s, const point_state *ps, double *feq, doub
 
 static void cell_point(const osim *s, int c, point_state *ps)
 {
-    double drho = (s->rhoA - s->rhoB) / (s->phiA - s->phiB);
+    real drho = (s->rhoA - s->rhoB) / (s->phiA - s->phiB);
     ps->phi = s->phi[c]; ps->rho = s->rho[c];
     ps->ux = s->u[0][c]; ps->uy = s->u[1][c]; ps->p = s->p[c];
     ps->mu = s->mu[c]; ps->lap_mu = s->lap_mu[c];
@@ -349,12 +367,12 @@ static void cell_auxiliaries(osim *s)
 #pragma omp parallel for schedule(static)
     for (int c = 0; c < N; c++) {
         point_state ps;
-        double feq[Q], geq[Q], Ff[Q], Fg[Q];
+        real feq[Q], geq[Q], Ff[Q], Fg[Q];
         cell_point(s, c, &ps);
         point_eq_src(s, &ps, feq, geq, Ff, Fg);
         for (int i = 0; i < Q; i++) {
-            double fb = oracle_bar_plus(s->f[i * N + c], feq[i], Ff[i], ps.tauf, s->dt);
-            double gb = oracle_bar_plus(s->g[i * N + c], geq[i], Fg[i], s->tau_g, s->dt);
+            real fb = oracle_bar_plus(s->f[i * N + c], feq[i], Ff[i], ps.tauf, s->dt);
+            real gb = oracle_bar_plus(s->g[i * N + c], geq[i], Fg[i], s->tau_g, s->dt);
             s->fbp[i * N + c] = fb;
             s->gbp[i * N + c] = gb;
             s->ftp[i * N + c] = oracle_tilde_plus(fb, s->f[i * N + c]);
@@ -371,27 +389,27 @@ static void cell_auxiliaries(osim *s)
    equilibria, sources and original distributions (Eq. original-function).
    aux holds the interpolated mu, lap mu, grad mu, grad p, grad phi. */
 typedef struct {
-    double mu, lap_mu, gmu[2], gp[2], gphi[2];
+    real mu, lap_mu, gmu[2], gp[2], gphi[2];
 } face_aux;
 
-static void face_originals(const osim *s, const double *fbar, const double *gbar, const face_aux *ax,
-                           int wall, double *forig, double *gorig)
+static void face_originals(const osim *s, const real *fbar, const real *gbar, const face_aux *ax,
+                           int wall, real *forig, real *gorig)
 {
-    double drho = (s->rhoA - s->rhoB) / (s->phiA - s->phiB);
+    real drho = (s->rhoA - s->rhoB) / (s->phiA - s->phiB);
     double h = s->h;
     point_state ps;
-    double phi = 0.0, sf = 0.0, mx = 0.0, my = 0.0;
+    real phi = 0.0, sf = 0.0, mx = 0.0, my = 0.0;
     for (int i = 0; i < Q; i++) {
         phi += gbar[i];
         sf += fbar[i];
         mx += XI[i][0] * fbar[i];
         my += XI[i][1] * fbar[i];
     }
-    double rho = rho_of(s, phi);
-    double Fx = -phi * ax->gmu[0] + (rho - s->rho_ref) * s->gx;
-    double Fy = -phi * ax->gmu[1] + (rho - s->rho_ref) * s->gy;
-    double grx = drho * ax->gphi[0], gry = drho * ax->gphi[1];
-    double ux, uy;
+    real rho = rho_of(s, phi);
+    real Fx = -phi * ax->gmu[0] + (rho - s->rho_ref) * s->gx;
+    real Fy = -phi * ax->gmu[1] + (rho - s->rho_ref) * s->gy;
+    real grx = drho * ax->gphi[0], gry = drho * ax->gphi[1];
+    real ux, uy;
     if (wall) {
         ux = 0.0;
         uy = 0.0;
@@ -399,12 +417,12 @@ static void face_originals(const osim *s, const double *fbar, const double *gbar
         ux = (mx + 0.5 * h * CS2 * Fx) / (CS2 * rho);
         uy = (my + 0.5 * h * CS2 * Fy) / (CS2 * rho);
     }
-    double p = sf + 0.5 * h * CS2 * (ux * grx + uy * gry - s->gamma * rho * s->lambda * ax->lap_mu);
+    real p = sf + 0.5 * h * CS2 * (ux * grx + uy * gry - s->gamma * rho * s->lambda * ax->lap_mu);
     ps.phi = phi; ps.rho = rho; ps.ux = ux; ps.uy = uy; ps.p = p;
     ps.mu = ax->mu; ps.lap_mu = ax->lap_mu; ps.Fx = Fx; ps.Fy = Fy;
     ps.grx = grx; ps.gry = gry; ps.gpx = ax->gp[0]; ps.gpy = ax->gp[1];
     ps.tauf = tauf_of(s, phi, rho);
-    double feq[Q], geq[Q], Ff[Q], Fg[Q];
+    real feq[Q], geq[Q], Ff[Q], Fg[Q];
     point_eq_src(s, &ps, feq, geq, Ff, Fg);
     for (int i = 0; i < Q; i++) {
         forig[i] = oracle_original(fbar[i], feq[i], Ff[i], ps.tauf, h);
@@ -422,17 +440,17 @@ static void interior_face(osim *s, int a, int iL, int jL, int iR, int jR)
     double dR = 0.5 * s->d[a][a == 0 ? iR : jR];
     double wL = dR / (dL + dR), wR = dL / (dL + dR);
     double area = a == 0 ? s->d[1][jL] : s->d[0][iL];
-    double fbar[Q], gbar[Q], forig[Q], gorig[Q];
+    real fbar[Q], gbar[Q], forig[Q], gorig[Q];
     /* step 3: bar-plus at x_b by linear interpolation, gradient sigma_b, then
        Eq. (fbar) with the Taylor form Eq. (fbar_h) */
     for (int i = 0; i < Q; i++) {
-        const double *Pf = s->fbp + i * N, *Pg = s->gbp + i * N;
-        double vf = wL * Pf[cL] + wR * Pf[cR];
-        double vg = wL * Pg[cL] + wR * Pg[cR];
-        double nf = (Pf[cR] - Pf[cL]) / (dL + dR);
-        double ng = (Pg[cR] - Pg[cL]) / (dL + dR);
-        double tf = wL * d1_dist(s, Pf, t, iL, jL) + wR * d1_dist(s, Pf, t, iR, jR);
-        double tg = wL * d1_dist(s, Pg, t, iL, jL) + wR * d1_dist(s, Pg, t, iR, jR);
+        const real *Pf = s->fbp + i * N, *Pg = s->gbp + i * N;
+        real vf = wL * Pf[cL] + wR * Pf[cR];
+        real vg = wL * Pg[cL] + wR * Pg[cR];
+        real nf = (Pf[cR] - Pf[cL]) / (dL + dR);
+        real ng = (Pg[cR] - Pg[cL]) / (dL + dR);
+        real tf = wL * d1_dist(s, Pf, t, iL, jL) + wR * d1_dist(s, Pf, t, iR, jR);
+        real tg = wL * d1_dist(s, Pg, t, iL, jL) + wR * d1_dist(s, Pg, t, iR, jR);
         fbar[i] = vf - s->h * (XI[i][a] * nf + XI[i][t] * tf);
         gbar[i] = vg - s->h * (XI[i][a] * ng + XI[i][t] * tg);
     }
@@ -463,12 +481,12 @@ static void wall_face(osim *s, int a, int i, int j, int side)
     int N = s->nx * s->ny, t = 1 - a, c = IDX(s, i, j);
     double dc = s->d[a][a == 0 ? i : j];
     double area = a == 0 ? s->d[1][j] : s->d[0][i];
-    double fbar[Q], gbar[Q], forig[Q], gorig[Q];
+    real fbar[Q], gbar[Q], forig[Q], gorig[Q];
     /* outgoing and parallel directions: Taylor reconstruction from the cell
        centre, x_b - xi h - x_c = (side dc/2 - xi_a h) e_a - xi_t h e_t */
     for (int q = 0; q < Q; q++) {
         if (XI[q][a] * side < 0) continue;
-        const double *Pf = s->fbp + q * N, *Pg = s->gbp + q * N;
+        const real *Pf = s->fbp + q * N, *Pg = s->gbp + q * N;
         double off = side * 0.5 * dc - s->h * XI[q][a];
         fbar[q] = Pf[c] + off * d1_dist(s, Pf, a, i, j) - s->h * XI[q][t] * d1_dist(s, Pf, t, i, j);
         gbar[q] = Pg[c] + off * d1_dist(s, Pg, a, i, j) - s->h * XI[q][t] * d1_dist(s, Pg, t, i, j);
@@ -505,8 +523,8 @@ static void wall_face(osim *s, int a, int i, int j, int side)
 static void all_faces(osim *s)
 {
     int nx = s->nx, ny = s->ny, N = nx * ny;
-    memset(s->Jf, 0, sizeof(double) * Q * N);
-    memset(s->Jg, 0, sizeof(double) * Q * N);
+    memset(s->Jf, 0, sizeof(real) * Q * N);
+    memset(s->Jg, 0, sizeof(real) * Q * N);
     /* x faces, one row at a time (rows touch disjoint cells) */
 #pragma omp parallel for schedule(static)
     for (int j = 0; j < ny; j++) {
@@ -554,7 +572,7 @@ void oracle_destroy(void *h);
 
 /* params: phiA, phiB, rhoA, rhoB, nuA, nuB, lambda, tau_g, beta, kappa, gx, gy, rho_ref, cfl */
 void *oracle_create(int nx, int ny, int bcx, int bcy, const double *dx, const double *dy,
-                    const double *prm)
+                    const real *prm)
 {
     if (nx < 1 || ny < 1) return NULL;
     osim *s = (osim *)calloc(1, sizeof(osim));
@@ -568,7 +586,7 @@ void *oracle_create(int nx, int ny, int bcx, int bcy, const double *dx, const do
     s->phiA = prm[0]; s->phiB = prm[1]; s->rhoA = prm[2]; s->rhoB = prm[3];
     s->nuA = prm[4]; s->nuB = prm[5]; s->lambda = prm[6]; s->tau_g = prm[7];
     s->beta = prm[8]; s->kappa = prm[9]; s->gx = prm[10]; s->gy = prm[11];
-    s->rho_ref = prm[12]; s->cfl = prm[13];
+    s->rho_ref = prm[12]; s->cfl = creal_or_same(prm[13]);
     /* Eq. (cfl): dt = alpha dx_min / C_max with C_max = sqrt(6 RT) */
     double dmin = dx[0];
     for (int i = 0; i < nx; i++) if (dx[i] < dmin) dmin = dx[i];
@@ -578,22 +596,22 @@ void *oracle_create(int nx, int ny, int bcx, int bcy, const double *dx, const do
     /* Eq. (kineticandmobility): lambda = c_s^2 tau_g eta */
     s->eta = s->lambda / (CS2 * s->tau_g);
     /* Eq. (Gama) with rho_r = rhoA / rhoB */
-    double rr = s->rhoA / s->rhoB;
+    real rr = s->rhoA / s->rhoB;
     s->gamma = (rr - 1.0) / (s->phiA - s->phiB * rr);
     s->muA = s->rhoA * s->nuA;
     s->muB = s->rhoB * s->nuB;
-    double **bufs[] = {&s->f, &s->g, &s->phi, &s->rho, &s->lap_phi, &s->mu, &s->lap_mu, &s->gphi[0],
+    real **bufs[] = {&s->f, &s->g, &s->phi, &s->rho, &s->lap_phi, &s->mu, &s->lap_mu, &s->gphi[0],
                        &s->gphi[1], &s->gmu[0], &s->gmu[1], &s->F[0], &s->F[1], &s->u[0], &s->u[1],
                        &s->p, &s->gp[0], &s->gp[1], &s->tauf};
     int nb = (int)(sizeof(bufs) / sizeof(bufs[0]));
     for (int k = 0; k < nb; k++) {
         int m = (k < 2) ? Q * N : N;
-        *bufs[k] = (double *)calloc((size_t)m, sizeof(double));
+        *bufs[k] = (real *)calloc((size_t)m, sizeof(real));
         if (!*bufs[k]) { oracle_destroy(s); return NULL; }
     }
-    double **qb[] = {&s->fbp, &s->gbp, &s->ftp, &s->gtp, &s->Jf, &s->Jg};
+    real **qb[] = {&s->fbp, &s->gbp, &s->ftp, &s->gtp, &s->Jf, &s->Jg};
     for (int k = 0; k < 6; k++) {
-        *qb[k] = (double *)calloc((size_t)Q * N, sizeof(double));
+        *qb[k] = (real *)calloc((size_t)Q * N, sizeof(real));
         if (!*qb[k]) { oracle_destroy(s); return NULL; }
     }
     return s;
@@ -603,7 +621,7 @@ void oracle_destroy(void *h)
 {
     osim *s = (osim *)h;
     if (!s) return;
-    double *all[] = {s->d[0], s->d[1], s->f, s->g, s->phi, s->rho, s->lap_phi, s->mu, s->lap_mu,
+    void *all[] = {s->d[0], s->d[1], s->f, s->g, s->phi, s->rho, s->lap_phi, s->mu, s->lap_mu,
                      s->gphi[0], s->gphi[1], s->gmu[0], s->gmu[1], s->F[0], s->F[1], s->u[0], s->u[1],
                      s->p, s->gp[0], s->gp[1], s->tauf, s->fbp, s->gbp, s->ftp, s->gtp, s->Jf, s->Jg};
     for (size_t k = 0; k < sizeof(all) / sizeof(all[0]); k++) free(all[k]);
@@ -615,7 +633,7 @@ double oracle_dt(void *h) { return ((osim *)h)->dt; }
 /* Step 1: from phi, u, p at the cells, the tilde distributions are
    tilde = eq - dt/2 F (Eq. auxf a with the original distribution at equilibrium).
    ux, uy, p may be NULL (zero). */
-int oracle_init(void *hd, const double *phi, const double *ux, const double *uy, const double *p)
+int oracle_init(void *hd, const real *phi, const real *ux, const real *uy, const real *p)
 {
     osim *s = (osim *)hd;
     int nx = s->nx, ny = s->ny, N = nx * ny;
@@ -648,7 +666,7 @@ int oracle_init(void *hd, const double *phi, const double *ux, const double *uy,
         }
     for (int c = 0; c < N; c++) {
         point_state ps;
-        double feq[Q], geq[Q], Ff[Q], Fg[Q];
+        real feq[Q], geq[Q], Ff[Q], Fg[Q];
         cell_point(s, c, &ps);
         point_eq_src(s, &ps, feq, geq, Ff, Fg);
         for (int i = 0; i < Q; i++) {
@@ -657,7 +675,7 @@ int oracle_init(void *hd, const double *phi, const double *ux, const double *uy,
         }
     }
     for (int c = 0; c < Q * N; c++)
-        if (!isfinite(s->f[c]) || !isfinite(s->g[c])) return -3;
+        if (!FINITE(s->f[c]) || !FINITE(s->g[c])) return -3;
     return 0;
 }
 
@@ -673,13 +691,13 @@ int oracle_step(void *hd, long n)
         update_cells(s);
     }
     for (int c = 0; c < Q * N; c++)
-        if (!isfinite(s->f[c]) || !isfinite(s->g[c])) return -3;
+        if (!FINITE(s->f[c]) || !FINITE(s->g[c])) return -3;
     return 0;
 }
 
 /* Macroscopic fields from the current tilde state (Eqs. phi, oderrho, u, P);
    any output pointer may be NULL. */
-void oracle_moments(void *hd, double *phi, double *rho, double *ux, double *uy, double *p)
+void oracle_moments(void *hd, real *phi, real *rho, real *ux, real *uy, real *p)
 {
     osim *s = (osim *)hd;
     int N = s->nx * s->ny;
@@ -694,8 +712,8 @@ void oracle_moments(void *hd, double *phi, double *rho, double *ux, double *uy, 
 }
 
 /* Cell fields of the last macro evaluation: mu, lap_mu, grad mu, grad p, grad phi, tau_f */
-void oracle_aux(void *hd, double *mu, double *lap_mu, double *gmux, double *gmuy, double *gpx,
-                double *gpy, double *gphix, double *gphiy, double *tauf)
+void oracle_aux(void *hd, real *mu, real *lap_mu, real *gmux, real *gmuy, real *gpx,
+                real *gpy, real *gphix, real *gphiy, real *tauf)
 {
     osim *s = (osim *)hd;
     int N = s->nx * s->ny;
@@ -712,32 +730,32 @@ void oracle_aux(void *hd, double *mu, double *lap_mu, double *gmux, double *gmuy
     }
 }
 
-void oracle_get_state(void *hd, double *f, double *g)
+void oracle_get_state(void *hd, real *f, real *g)
 {
     osim *s = (osim *)hd;
     size_t n = (size_t)Q * s->nx * s->ny;
-    memcpy(f, s->f, n * sizeof(double));
-    memcpy(g, s->g, n * sizeof(double));
+    memcpy(f, s->f, n * sizeof(real));
+    memcpy(g, s->g, n * sizeof(real));
 }
 
-void oracle_set_state(void *hd, const double *f, const double *g)
+void oracle_set_state(void *hd, const real *f, const real *g)
 {
     osim *s = (osim *)hd;
     size_t n = (size_t)Q * s->nx * s->ny;
-    memcpy(s->f, f, n * sizeof(double));
-    memcpy(s->g, g, n * sizeof(double));
+    memcpy(s->f, f, n * sizeof(real));
+    memcpy(s->g, g, n * sizeof(real));
 }
 
 /* Volume-weighted totals of phi and rho (Eq. locallyconserved) */
-void oracle_conservation(void *hd, double *sum_phi, double *sum_rho)
+void oracle_conservation(void *hd, real *sum_phi, real *sum_rho)
 {
     osim *s = (osim *)hd;
     int nx = s->nx, ny = s->ny, N = nx * ny;
-    double a = 0.0, b = 0.0;
+    real a = 0.0, b = 0.0;
     for (int j = 0; j < ny; j++)
         for (int i = 0; i < nx; i++) {
             int c = IDX(s, i, j);
-            double phi = 0.0;
+            real phi = 0.0;
             for (int q = 0; q < Q; q++) phi += s->g[q * N + c];
             double vol = s->d[0][i] * s->d[1][j];
             a += vol * phi;
@@ -748,7 +766,7 @@ void oracle_conservation(void *hd, double *sum_phi, double *sum_rho)
 }
 
 /* Non-uniform first and second derivative of a cell field (mirror ghosts), for pins */
-void oracle_derivatives(void *hd, const double *F, double *dx, double *dy, double *lap)
+void oracle_derivatives(void *hd, const real *F, real *dx, real *dy, real *lap)
 {
     osim *s = (osim *)hd;
     for (int j = 0; j < s->ny; j++)
@@ -761,17 +779,17 @@ void oracle_derivatives(void *hd, const double *F, double *dx, double *dy, doubl
 }
 
 /* Cell-centre bar-plus distributions of the current state (step 2), [Q][N] each */
-void oracle_bar_plus_fields(void *hd, double *fbp, double *gbp)
+void oracle_bar_plus_fields(void *hd, real *fbp, real *gbp)
 {
     osim *s = (osim *)hd;
     size_t n = (size_t)Q * s->nx * s->ny;
     cell_macros(s);
     cell_auxiliaries(s);
-    if (fbp) memcpy(fbp, s->fbp, n * sizeof(double));
-    if (gbp) memcpy(gbp, s->gbp, n * sizeof(double));
+    if (fbp) memcpy(fbp, s->fbp, n * sizeof(real));
+    if (gbp) memcpy(gbp, s->gbp, n * sizeof(real));
 }
 
-void oracle_derived(void *hd, double *out /* dt, h, eta, gamma, muA, muB */)
+void oracle_derived(void *hd, real *out /* dt, h, eta, gamma, muA, muB */)
 {
     osim *s = (osim *)hd;
     out[0] = s->dt; out[1] = s->h; out[2] = s->eta; out[3] = s->gamma; out[4] = s->muA; out[5] = s->muB;

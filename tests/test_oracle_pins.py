@@ -199,3 +199,38 @@ def test_derived_parameters():
     assert d["eta"] == pytest.approx(0.2 / (0.4 / 3.0), rel=1e-15)
     assert d["gamma"] == pytest.approx((3.0 - 1.0) / (1.0 - 0.0), rel=1e-15)
     assert d["muA"] == pytest.approx(0.3) and d["muB"] == pytest.approx(0.2)
+
+
+def test_complex_step_build_matches_real_build_and_central_differences():
+    """The double-complex oracle (complex step) reproduces the real oracle's values
+    exactly and its derivatives agree with central differences of the real oracle."""
+    mesh = I.Mesh(1.0 + 0.2 * np.sin(np.arange(12)), np.ones(10), I.PERIODIC, I.WALL)
+    beta, kappa = I.params_from_sigma_width(1e-2, 3.0)
+    prm = I.Params(rhoA=2.0, rhoB=1.0, nuA=0.1, nuB=0.2, mobility=0.3, beta=beta, kappa=kappa, gy=-1e-4, rho_ref=1.5)
+    phi0 = I.drop_field(mesh, 3.0, (6.0, 5.0), 3.0)
+    steps = 6
+    target = np.full(phi0.shape, 0.3)
+    o = oracle.Oracle(mesh, prm).init(phi0)
+    o.step(steps)
+    cs = oracle.OracleCS(mesh, prm.as_list()).init(phi0).step(steps)
+    np.testing.assert_array_equal(cs.phi().real, o.moments()["phi"])
+
+    def L(p, phi):
+        r = oracle.Oracle(mesh, p).init(phi)
+        r.step(steps)
+        d = r.moments()["phi"] - target
+        return np.sum(d * d)
+
+    rng = np.random.default_rng(9)
+    v = rng.standard_normal(phi0.shape)
+    g = oracle.complex_step_gradient(mesh, prm, phi0, steps, target, direction_phi0=v, which=("kappa", "mobility"))
+    for name in ("kappa", "mobility"):
+        eps = 1e-5 * getattr(prm, name)
+        pp, pm = I.Params(**vars(prm)), I.Params(**vars(prm))
+        setattr(pp, name, getattr(prm, name) + eps)
+        setattr(pm, name, getattr(prm, name) - eps)
+        fd = (L(pp, phi0) - L(pm, phi0)) / (2 * eps)
+        assert g[name] == pytest.approx(fd, rel=1e-5)
+    eps = 1e-6
+    fd = (L(prm, phi0 + eps * v) - L(prm, phi0 - eps * v)) / (2 * eps)
+    assert g["phi0_dir"] == pytest.approx(fd, rel=1e-6)
