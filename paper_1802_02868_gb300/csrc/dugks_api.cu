@@ -16,6 +16,7 @@
 #include "dugks_common.cuh"
 #include "dugks_kernels.cuh"
 #include "dugks_fused.cuh"
+#include "dugks_adjoint.cuh"
 
 using namespace dugks;
 
@@ -61,6 +62,8 @@ struct dugks_sim {
     double2 *d_partials = nullptr;
     double2 *d_sums = nullptr;
     double *d_stage = nullptr;    // dense FP64 staging [5][n_dense]
+    double *d_init_in = nullptr;  // the last init inputs phi, ux, uy, p [4][n_dense] (for the adjoint)
+    bool has_init = false;
     Planes<double> P64{};
     Planes<float> P32{};
     long launches = 0;
@@ -509,6 +512,7 @@ void free_sim(dugks_sim *s)
     cudaFree(s->d_partials);
     cudaFree(s->d_sums);
     cudaFree(s->d_stage);
+    cudaFree(s->d_init_in);
     if (s->graph2) cudaGraphExecDestroy(s->graph2);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     for (auto &e : s->ev_used) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
@@ -531,9 +535,178 @@ int sync_status(dugks_sim *s)
     return DUGKS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint: checkpointed forward, then the reverse sweep of dugks_adjoint.cuh
+// ---------------------------------------------------------------------------
+template <typename T>
+struct AdjWork {
+    size_t fg_bytes = 0, phi_bytes = 0, state_bytes = 0;
+    void *mem = nullptr;
+    unsigned char *ckpt = nullptr, *seg = nullptr;
+    T *x0 = nullptr, *x1 = nullptr, *bp = nullptr, *scal = nullptr, *fbp = nullptr;
+    double *pk = nullptr, *loss = nullptr, *target = nullptr, *phi0b = nullptr;
+};
+
+template <typename T>
+void copy_state(dugks_sim *s, void *dst_fg, void *dst_phi, const void *src_fg, const void *src_phi, size_t fg_bytes,
+                size_t phi_bytes)
+{
+    cudaMemcpyAsync(dst_fg, src_fg, fg_bytes, cudaMemcpyDeviceToDevice, s->stream);
+    cudaMemcpyAsync(dst_phi, src_phi, phi_bytes, cudaMemcpyDeviceToDevice, s->stream);
+}
+
+template <typename T>
+int adjoint_impl(dugks_sim *s, long nsteps, int K, const double *target_h, double *loss_h, double *phi0b_h,
+                 double *dkappa_h, double *dlambda_h)
+{
+    Planes<T> &P = planes<T>(s);
+    const long long N = P.N, D = s->n_dense;
+    const int n = s->n_inst;
+    const dim3 blk(TX, TY);
+    const unsigned g = (unsigned)s->n_tiles;
+    AdjWork<T> w;
+    w.fg_bytes = sizeof(T) * 2 * Q * (size_t)N;
+    w.phi_bytes = sizeof(phi_t<T>) * (size_t)N;
+    w.state_bytes = w.fg_bytes + w.phi_bytes;
+    const long nck = (nsteps + K - 1) / K;   // checkpoints 0 .. nck (the last is the final state)
+    const size_t scal_planes = 13;
+    const size_t bytes = w.state_bytes * (size_t)(nck + 1 + K) + sizeof(T) * (size_t)N * (2 * 2 * Q + 2 * Q + scal_planes + 2 * Q)
+                       + sizeof(double) * (size_t)(2 * n + n + 2 * D);
+    cudaError_t e = cudaMalloc(&w.mem, bytes);
+    if (e != cudaSuccess) return cuda_status(e);
+    unsigned char *m = (unsigned char *)w.mem;
+    w.ckpt = m; m += w.state_bytes * (size_t)(nck + 1);
+    w.seg = m; m += w.state_bytes * (size_t)K;
+    w.x0 = (T *)m; m += w.fg_bytes;
+    w.x1 = (T *)m; m += w.fg_bytes;
+    w.bp = (T *)m; m += sizeof(T) * 2 * Q * (size_t)N;
+    w.scal = (T *)m; m += sizeof(T) * scal_planes * (size_t)N;
+    w.fbp = (T *)m; m += sizeof(T) * 2 * Q * (size_t)N;
+    w.pk = (double *)m; m += sizeof(double) * 2 * n;
+    w.loss = (double *)m; m += sizeof(double) * n;
+    w.target = (double *)m; m += sizeof(double) * D;
+    w.phi0b = (double *)m;
+    T *save_fbp = P.fbp, *save_gbp = P.gbp;
+    P.fbp = w.fbp;
+    P.gbp = w.fbp + (size_t)Q * N;
+    const bool timing = s->timing;
+    s->timing = false;
+    auto st_fg = [&](long k) { return (void *)(w.ckpt + w.state_bytes * (size_t)k); };
+    auto st_phi = [&](long k) { return (void *)(w.ckpt + w.state_bytes * (size_t)k + w.fg_bytes); };
+    auto sg_fg = [&](long k) { return (void *)(w.seg + w.state_bytes * (size_t)k); };
+    auto sg_phi = [&](long k) { return (void *)(w.seg + w.state_bytes * (size_t)k + w.fg_bytes); };
+    int rc = DUGKS_OK;
+    // forward from the saved init inputs, with checkpoints
+    e = cudaMemcpyAsync(s->d_stage, s->d_init_in, sizeof(double) * 4 * D, cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_status, 0, sizeof(int) * n, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(w.target, target_h, sizeof(double) * D, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.pk, 0, sizeof(double) * 3 * n, s->stream);
+    if (e != cudaSuccess) rc = cuda_status(e);
+    if (!rc) rc = do_init<T>(s);
+    for (long c = 0; c < nck && !rc; c++) {
+        copy_state<T>(s, st_fg(c), st_phi(c), P.f, P.phi, w.fg_bytes, w.phi_bytes);
+        rc = dugks_step(s, std::min<long>(K, nsteps - c * K));
+    }
+    if (!rc) copy_state<T>(s, st_fg(nck), st_phi(nck), P.f, P.phi, w.fg_bytes, w.phi_bytes);
+    // loss and the seed adjoint
+    T *xb = w.x0, *xn = w.x1;
+    if (!rc) {
+        ka_seed<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, P, xb, xb + (size_t)Q * N, w.target, s->d_dense0, w.loss);
+        s->launches++;
+    }
+    AdjPlanes<T> A;
+    A.N = N;
+    A.pk = w.pk;
+    T *sc = w.scal;
+    A.phi = sc; A.mu = sc + N; A.lapmu = sc + 2 * N; A.gmx = sc + 3 * N; A.gmy = sc + 4 * N; A.gfx = sc + 5 * N;
+    A.gfy = sc + 6 * N; A.gpx = sc + 7 * N; A.gpy = sc + 8 * N; A.p = sc + 9 * N; A.ux = sc + 10 * N; A.uy = sc + 11 * N;
+    A.lapphi = sc + 12 * N;
+    A.bp = w.bp;
+    // reverse sweep, one checkpoint segment at a time
+    for (long c = nck - 1; c >= 0 && !rc; c--) {
+        const long len = std::min<long>(K, nsteps - c * K);
+        copy_state<T>(s, P.f, P.phi, st_fg(c), st_phi(c), w.fg_bytes, w.phi_bytes);
+        for (long k = 0; k < len && !rc; k++) {
+            copy_state<T>(s, sg_fg(k), sg_phi(k), P.f, P.phi, w.fg_bytes, w.phi_bytes);
+            if (k + 1 < len) rc = dugks_step(s, 1);
+        }
+        for (long k = len - 1; k >= 0 && !rc; k--) {
+            copy_state<T>(s, P.f, P.phi, sg_fg(k), sg_phi(k), w.fg_bytes, w.phi_bytes);
+            k_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P);
+            k_macro<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, 0);
+            k_cell<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P);
+            cudaMemsetAsync(w.bp, 0, sizeof(T) * 2 * Q * (size_t)N, s->stream);
+            cudaMemsetAsync(w.scal, 0, sizeof(T) * scal_planes * (size_t)N, s->stream);
+            A.xf = xb; A.xg = xb + (size_t)Q * N;
+            A.af = xn; A.ag = xn + (size_t)Q * N;
+            ka_face<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, A);
+            ka_cell<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, A);
+            ka_macro<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, A);
+            ka_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, A);
+            ka_phi<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, A, nullptr, s->d_dense0);
+            s->launches += 8;
+            std::swap(xb, xn);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) rc = cuda_status(e);
+        }
+    }
+    // the initialisation: planes hold phi0, u0, p0 and mu(phi0)
+    if (!rc) {
+        const dim3 b2(TX, TY);
+        k_unpack_phi<phi_t<T>><<<g, b2, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_init_in, P.phi, s->d_dense0);
+        k_unpack<T><<<g, b2, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_init_in + D, P.ux, s->d_dense0);
+        k_unpack<T><<<g, b2, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_init_in + 2 * D, P.uy, s->d_dense0);
+        k_unpack<T><<<g, b2, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_init_in + 3 * D, P.p, s->d_dense0);
+        k_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P);
+        cudaMemsetAsync(w.scal, 0, sizeof(T) * scal_planes * (size_t)N, s->stream);
+        A.xf = xb; A.xg = xb + (size_t)Q * N;
+        ka_init<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, A);
+        ka_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, A);
+        ka_phi<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, A, w.phi0b, s->d_dense0);
+        s->launches += 8;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) rc = cuda_status(e);
+    }
+    // leave the simulation at the final state of the forward run
+    if (!rc) copy_state<T>(s, P.f, P.phi, st_fg(nck), st_phi(nck), w.fg_bytes, w.phi_bytes);
+    std::vector<double> pk(2 * n), loss(n);
+    if (!rc) {
+        e = cudaMemcpyAsync(pk.data(), w.pk, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(loss.data(), w.loss, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess && phi0b_h) e = cudaMemcpyAsync(phi0b_h, w.phi0b, sizeof(double) * D, cudaMemcpyDeviceToHost, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) rc = cuda_status(e);
+    }
+    if (!rc) {
+        for (int k = 0; k < n; k++) {
+            if (loss_h) loss_h[k] = loss[k];
+            if (dlambda_h) dlambda_h[k] = pk[2 * k];
+            if (dkappa_h) dkappa_h[k] = pk[2 * k + 1];
+        }
+        rc = sync_status(s);
+    }
+    cudaStreamSynchronize(s->stream);
+    P.fbp = save_fbp;
+    P.gbp = save_gbp;
+    s->timing = timing;
+    cudaFree(w.mem);
+    return rc;
+}
+
 }  // namespace
 
 extern "C" {
+
+int dugks_adjoint(dugks_sim *s, long nsteps, int ckpt_every, const double *phi_target, double *loss, double *dL_dphi0,
+                  double *dL_dkappa, double *dL_dlambda)
+{
+    if (!s || !phi_target || nsteps < 1 || ckpt_every < 1) return DUGKS_ERR_ARG;
+    if (!s->has_init) return DUGKS_ERR_ARG;
+    const int K = (int)std::min<long>(ckpt_every, nsteps);
+    return s->prec == DUGKS_FP64 ? adjoint_impl<double>(s, nsteps, K, phi_target, loss, dL_dphi0, dL_dkappa, dL_dlambda)
+                                 : adjoint_impl<float>(s, nsteps, K, phi_target, loss, dL_dphi0, dL_dkappa, dL_dlambda);
+}
+
 
 int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *params, void *cuda_stream, dugks_sim **out)
 {
@@ -647,6 +820,7 @@ int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *para
     chk(cudaMalloc(&s->d_partials, sizeof(double2) * tiles.size()));
     chk(cudaMalloc(&s->d_sums, sizeof(double2) * n));
     chk(cudaMalloc(&s->d_stage, sizeof(double) * (size_t)std::max<long long>(5, 2 * Q) * (size_t)dense));
+    chk(cudaMalloc(&s->d_init_in, sizeof(double) * 4 * (size_t)dense));
     if (e != cudaSuccess) {
         int rc = cuda_status(e);
         free_sim(s);
@@ -697,9 +871,11 @@ int dugks_init(dugks_sim *s, const double *phi, const double *ux, const double *
         else e = cudaMemsetAsync(s->d_stage + k * D, 0, sizeof(double) * D, s->stream);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(s->d_status, 0, sizeof(int) * s->n_inst, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_init_in, s->d_stage, sizeof(double) * 4 * D, cudaMemcpyDeviceToDevice, s->stream);
     if (e != cudaSuccess) return cuda_status(e);
     int rc = s->prec == DUGKS_FP64 ? do_init<double>(s) : do_init<float>(s);
     if (rc) return rc;
+    s->has_init = true;
     return sync_status(s);
 }
 

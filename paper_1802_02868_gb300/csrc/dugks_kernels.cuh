@@ -69,9 +69,8 @@ struct PtInv {
 };
 
 template <typename T>
-__device__ __forceinline__ PtInv<T> pt_inv(const InstDev &I, const Pt<T> &s)
+__device__ __forceinline__ PtInv<T> pt_inv_p(const ParT<T> &Pr, const Pt<T> &s)
 {
-    const ParT<T> &Pr = par<T>(I);
     const T cs2 = Cst<T>::cs2;
     PtInv<T> v;
     v.uu15 = T(1.5) * (s.ux * s.ux + s.uy * s.uy);
@@ -84,6 +83,12 @@ __device__ __forceinline__ PtInv<T> pt_inv(const InstDev &I, const Pt<T> &s)
     v.cgx = cs2 * s.grx;
     v.cgy = cs2 * s.gry;
     return v;
+}
+
+template <typename T>
+__device__ __forceinline__ PtInv<T> pt_inv(const InstDev &I, const Pt<T> &s)
+{
+    return pt_inv_p<T>(par<T>(I), s);
 }
 
 // f^eq_q, g^eq_q (Eqs. feq, geq, su, Hi) and F^f_q, F^g_q (Eqs. F, G)

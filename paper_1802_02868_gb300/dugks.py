@@ -52,7 +52,8 @@ EXPORTS = ("dugks_create", "dugks_batch_create", "dugks_destroy", "dugks_init", 
            "dugks_conservation", "dugks_batch_status", "dugks_dt", "dugks_info", "dugks_save", "dugks_load",
            "dugks_launch_count", "dugks_set_timing", "dugks_kernel_times", "dugks_kernel_name",
            "dugks_kernel_bytes_per_cell", "dugks_status_str", "dugks_conservation_static",
-           "dugks_autotune", "dugks_set_tile_shape", "dugks_tile_shape", "dugks_tile_shape_name")
+           "dugks_autotune", "dugks_set_tile_shape", "dugks_tile_shape", "dugks_tile_shape_name",
+           "dugks_adjoint")
 STATIC_MAX_CELLS = 16777216
 
 
@@ -92,6 +93,7 @@ def load(build_if_missing: bool = True):
     L.dugks_kernel_name.restype = ctypes.c_char_p
     L.dugks_kernel_bytes_per_cell.argtypes = [vp, ip, dp]
     L.dugks_conservation_static.argtypes = [vp, vp, vp, ip, ip] + [ctypes.c_double] * 4 + [vp, vp]
+    L.dugks_adjoint.argtypes = [vp, ctypes.c_long, ip, dp, dp, dp, dp, dp]
     L.dugks_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), dp]
     L.dugks_set_tile_shape.argtypes = [vp, ip]
     L.dugks_tile_shape.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int)] * 3
@@ -254,6 +256,22 @@ class Sim:
         n = (ctypes.c_long * NUM_KERNELS)()
         _check("dugks_kernel_times", load().dugks_kernel_times(self.h, _dp(ms), n))
         return {kernel_name(k): (ms[k], n[k]) for k in range(NUM_KERNELS)}
+
+    def adjoint(self, nsteps, phi_target, ckpt_every=100):
+        """Gradient of L = sum_cells (phi_T - phi_target)^2 after ``nsteps`` steps
+        from the last ``init`` inputs, by the library's reverse sweep with
+        checkpoints every ``ckpt_every`` steps.  Returns a dict with ``loss``,
+        ``dphi0`` (field(s) like the init phi), ``dkappa`` and ``dlambda``
+        (per instance for a batch, scalars for one simulation)."""
+        n = len(self.meshes)
+        tgt = self._cat(phi_target)
+        loss, dk, dl = np.zeros(n), np.zeros(n), np.zeros(n)
+        dphi = np.zeros(self.ncells)
+        _check("dugks_adjoint", load().dugks_adjoint(self.h, int(nsteps), int(ckpt_every), _dp(tgt), _dp(loss),
+                                                      _dp(dphi), _dp(dk), _dp(dl)))
+        if self.single:
+            return {"loss": loss[0], "dphi0": self._split(dphi), "dkappa": dk[0], "dlambda": dl[0]}
+        return {"loss": loss, "dphi0": self._split(dphi), "dkappa": dk, "dlambda": dl}
 
     def autotune(self, steps=5):
         """Time every tile shape of the fused step on the current state (which is
