@@ -82,6 +82,23 @@ def workload(name, seed):
     return cases, desc
 
 
+def max_over_ranks(x, dist, device):
+    """Largest value of x over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world_size, seconds):
+    """Whole-job throughput: every rank advances its own workload (weak
+    scaling), so the job processes world_size times the per-rank units in the
+    slowest rank's time."""
+    return world_size * units_per_rank / seconds
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -196,6 +213,43 @@ def fp64_single_instance_rate(dugks, torch, cases, n_sample=16, steps=3):
     return cell_updates / (total_ms * 1e-3), len(idx)
 
 
+def run_adjoint(args, dugks, torch):
+    """Adjoint workload: Rayleigh-Taylor 256x512, 4000 steps, FP32 forward with
+    a checkpoint every 100 steps and recomputation; gradient of the squared L2
+    misfit of phi against a seeded target with respect to the initial phi field,
+    kappa and the mobility.  Compared with the 20 FP64 forward runs that central
+    differences of the same 10 parameters (8 amplitudes, kappa, mobility) need,
+    timed on one FP64 run."""
+    nx, ny, nsteps, K = 256, 512, args.adjoint_steps, 100
+    rng = np.random.default_rng(1803)
+    amps = np.concatenate([[0.1 * nx], rng.normal(0.0, 0.01 * nx, 7)])
+    c = I.rayleigh_taylor(nx=nx, ny=ny, amplitudes=list(amps))
+    tgt = I.rt_field(c.mesh, float(nx), 0.5 * ny, list(amps + rng.normal(0.0, 0.01 * nx, 8)), 4.0)
+    prec = dugks.FP32 if args.precision == "fp32" else dugks.FP64
+    sim = dugks.Sim(c.mesh, c.params, prec).init(c.phi0)
+    sim.adjoint(min(nsteps, 200), tgt, ckpt_every=K)     # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = sim.adjoint(nsteps, tgt, ckpt_every=K)
+    t_adj = time.perf_counter() - t0
+    s64 = dugks.Sim(c.mesh, c.params, dugks.FP64).init(c.phi0)
+    s64.step(20)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s64.step(nsteps)
+    torch.cuda.synchronize()
+    t_fwd64 = time.perf_counter() - t0
+    line = {"metric": "adjoint gradient wall time (10 parameters + dL/dphi0)", "value": t_adj, "unit": "s",
+            "n_gpus": 1, "steps": nsteps, "warmup": 1, "higher_is_better": False, "dtype": args.precision,
+            "data": "synthetic", "config": {"workload": "adjoint: Rayleigh-Taylor %dx%d, %d steps, checkpoint every %d, "
+                                                        "8 cosine amplitudes (seed 1803)" % (nx, ny, nsteps, K)},
+            "loss": float(r["loss"]), "dkappa": float(r["dkappa"]), "dlambda": float(r["dlambda"]),
+            "fp64_forward_s": t_fwd64, "fd20_fp64_s": 20 * t_fwd64, "speedup_vs_fd20_fp64": 20 * t_fwd64 / t_adj,
+            "forward_equivalent_cell_updates_per_s": nsteps * nx * ny / t_adj}
+    print(json.dumps(line))
+    return 0
+
+
 def run_reference(args, cases, desc):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -236,10 +290,16 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--adjoint", action="store_true", help="time the adjoint workload instead")
+    ap.add_argument("--adjoint-steps", type=int, default=4000)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
     ws, rank, local = dist_env()
+    if args.adjoint:
+        import torch
+        from paper_1802_02868_gb300 import dugks
+        return run_adjoint(args, dugks, torch)
     cases, desc = workload(args.workload, 1802 + rank)
     if args.impl == "reference":
         return run_reference(args, cases, desc)
@@ -288,15 +348,12 @@ def main():
     ktimes = sim.kernel_times()
     sim.set_timing(False)
     clk = clocks.stop()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     st = sim.status()
     n_finite = sum(1 for v in st if v == 0)
     # masked (non-finite) instances do no work: count only the cells advanced
     live_cells = int(sum(c.mesh.ncells for c, v in zip(cases, st) if v == 0))
-    value = ws * args.steps * live_cells / (ms * 1e-3)
+    value = job_rate(args.steps * live_cells, ws, ms * 1e-3)
 
     # ---- end to end through the public API: host phi -> init -> steps with a
     # per-step FP64 conservation read-back -> moments to host
@@ -314,14 +371,11 @@ def main():
         out_h[k].numpy()[:] = arr
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist, "cuda")
     n_inst = len(cases)
     h2d = ncells * 8 / args.steps
     d2h = (2 * 8 * n_inst * args.steps + 5 * 8 * ncells) / args.steps
-    e2e = {"value": ws * args.steps * ncells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+    e2e = {"value": job_rate(args.steps * ncells, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h,
            "note": "init from pinned host phi + K steps each followed by a conservation read-back + moments to host"}
 
