@@ -320,15 +320,68 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
     constexpr int NT = BX * BY;
     const long long N = io.N;
 
+    // global index of every region column and row (wrapped on periodic axes,
+    // -1 outside the domain), kept in shared memory for all later phases
+    for (int r = tid; r < L::NG; r += NT) {
+        const bool isx = r < L::W4;
+        const int n = isx ? I.nx : I.ny;
+        int g = (isx ? i0 : j0) + (isx ? r - 4 : r - L::W4 - 4);
+        if ((isx ? I.bcx : I.bcy) == 0) {
+            while (g < 0) g += n;
+            while (g >= n) g -= n;
+        } else if (g < 0 || g >= n) {
+            g = -1;
+        }
+        S.gg[r] = g;
+    }
+    __syncthreads();
+    auto gpos = [&](bool isx, int pos) -> int { return S.gg[isx ? pos + 4 : L::W4 + pos + 4]; };
+    auto cell = [&](int gi, int gj) -> long long { return I.cell0 + (long long)gj * I.nxp + gi; };
+
+    // ---- phase 1: asynchronous copies of phi (R4), then of tilde f (R2) and
+    // tilde g (R1); positions outside the domain are zero-filled.  They are
+    // issued first so that their latency overlaps the geometry set-up.
+    for (int r = tid; r < L::A4; r += NT) {
+        const int gi = gpos(true, r % L::W4 - 4), gj = gpos(false, r / L::W4 - 4);
+        if (gi >= 0 && gj >= 0) {
+            cp_async<sizeof(phi_t<T>)>(S.phi + r, io.phi_in + cell(gi, gj));
+        } else {
+            phi_t<T> v;
+            phi_from_zero(v);
+            S.phi[r] = v;
+        }
+    }
+    cp_commit();
+    for (int r = tid; r < L::A2; r += NT) {
+        const int gi = gpos(true, r % L::W2 - 2), gj = gpos(false, r / L::W2 - 2);
+        if (gi >= 0 && gj >= 0) {
+            const long long c = cell(gi, gj);
+#pragma unroll
+            for (int q = 0; q < Q; q++) cp_async<sizeof(T)>(S.sf + q * L::A2 + r, io.f_in + q * N + c);
+        } else {
+#pragma unroll
+            for (int q = 0; q < Q; q++) S.sf[q * L::A2 + r] = T(0);
+        }
+    }
+    for (int r = tid; r < L::A1; r += NT) {
+        const int gi = gpos(true, r % L::W1 - 1), gj = gpos(false, r / L::W1 - 1);
+        if (gi >= 0 && gj >= 0) {
+            const long long c = cell(gi, gj);
+#pragma unroll
+            for (int q = 0; q < Q; q++) cp_async<sizeof(T)>(S.sg + q * L::A1 + r, io.g_in + q * N + c);
+        } else {
+#pragma unroll
+            for (int q = 0; q < Q; q++) S.sg[q * L::A1 + r] = T(0);
+        }
+    }
+    cp_commit();
+
     // ---- geometry of the region columns and rows (SoA)
     for (int r = tid; r < L::NG; r += NT) {
         const bool isx = r < L::W4;
         const int pos = isx ? r - 4 : r - L::W4 - 4;
-        const int n = isx ? I.nx : I.ny;
-        const bool per = (isx ? I.bcx : I.bcy) == 0;
-        int g = (isx ? i0 : j0) + pos;
-        if (per) g = ((g % n) + n) % n;
-        else if (g < 0 || g >= n) g = -1;
+        const int g = S.gg[r];
+        (void)pos;
         T v[11];
         int fl = 0;
         if (g >= 0) {
@@ -343,51 +396,8 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
         }
 #pragma unroll
         for (int k = 0; k < 11; k++) S.ga[k * L::NG + r] = v[k];
-        S.gg[r] = g;
         S.gf[r] = fl;
     }
-    __syncthreads();
-    auto cell = [&](int gi, int gj) -> long long { return I.cell0 + (long long)gj * I.nxp + gi; };
-
-    // ---- phase 1: asynchronous copies of phi (R4), then of tilde f (R2) and
-    // tilde g (R1); positions outside the domain are zero-filled
-    for (int r = tid; r < L::A4; r += NT) {
-        const int x = r % L::W4 - 4, y = r / L::W4 - 4;
-        const int gi = S.gidx(0, x), gj = S.gidx(1, y);
-        if (gi >= 0 && gj >= 0) {
-            cp_async<sizeof(phi_t<T>)>(S.phi + r, io.phi_in + cell(gi, gj));
-        } else {
-            phi_t<T> v;
-            phi_from_zero(v);
-            S.phi[r] = v;
-        }
-    }
-    cp_commit();
-    for (int r = tid; r < L::A2; r += NT) {
-        const int x = r % L::W2 - 2, y = r / L::W2 - 2;
-        const int gi = S.gidx(0, x), gj = S.gidx(1, y);
-        if (gi >= 0 && gj >= 0) {
-            const long long c = cell(gi, gj);
-#pragma unroll
-            for (int q = 0; q < Q; q++) cp_async<sizeof(T)>(S.sf + q * L::A2 + r, io.f_in + q * N + c);
-        } else {
-#pragma unroll
-            for (int q = 0; q < Q; q++) S.sf[q * L::A2 + r] = T(0);
-        }
-    }
-    for (int r = tid; r < L::A1; r += NT) {
-        const int x = r % L::W1 - 1, y = r / L::W1 - 1;
-        const int gi = S.gidx(0, x), gj = S.gidx(1, y);
-        if (gi >= 0 && gj >= 0) {
-            const long long c = cell(gi, gj);
-#pragma unroll
-            for (int q = 0; q < Q; q++) cp_async<sizeof(T)>(S.sg + q * L::A1 + r, io.g_in + q * N + c);
-        } else {
-#pragma unroll
-            for (int q = 0; q < Q; q++) S.sg[q * L::A1 + r] = T(0);
-        }
-    }
-    cp_commit();
     cp_wait<1>();   // phi has landed
     __syncthreads();
 
@@ -515,6 +525,19 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
     }
     __syncthreads();
 
+    // the tile cell's own tilde f and g for the update: loaded now so that
+    // their latency overlaps the face work
+    const int x = threadIdx.x, y = threadIdx.y;
+    const int gi = i0 + x, gj = j0 + y;
+    const bool own = gi < I.nx && gj < I.ny;
+    const long long c = own ? cell(gi, gj) : 0;
+    T fo[Q], go[Q];
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+        fo[q] = own ? io.f_in[q * N + c] : T(0);
+        go[q] = own ? io.g_in[q * N + c] : T(0);
+    }
+
     // ---- phase 5: every face of the tile once (x faces first in the index space)
     for (int k = tid; k < L::NFT; k += NT) {
         T Ff[6], Fg[6];
@@ -526,9 +549,7 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
     __syncthreads();
 
     // ---- phase 6: update of the tile cell (Eqs. relations2, updatef)
-    const int x = threadIdx.x, y = threadIdx.y;
-    const int gi = i0 + x, gj = j0 + y;
-    if (gi >= I.nx || gj >= I.ny) return;
+    if (!own) return;
     T Jf[Q], Jg[Q];
     Jf[0] = 0; Jg[0] = 0;
     {
@@ -545,7 +566,6 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
             Jg[qy] += S.flux[(6 + m) * L::NFT + kn] - S.flux[(6 + m) * L::NFT + ks];
         }
     }
-    const long long c = cell(gi, gj);
     const int r1 = TL::i1(x, y);
     const T dtv = dt / (S.c(10, 0, x) * S.c(10, 1, y));
     bool finite = true;
@@ -553,8 +573,8 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
         T phi = 0;
 #pragma unroll
         for (int q = 0; q < Q; q++) {
-            const T fn = T(4.0 / 3.0) * S.bp[q * L::A1 + r1] - T(1.0 / 3.0) * io.f_in[q * N + c] - dtv * Jf[q];
-            const T gn = T(4.0 / 3.0) * S.bp[(Q + q) * L::A1 + r1] - T(1.0 / 3.0) * io.g_in[q * N + c] - dtv * Jg[q];
+            const T fn = T(4.0 / 3.0) * S.bp[q * L::A1 + r1] - T(1.0 / 3.0) * fo[q] - dtv * Jf[q];
+            const T gn = T(4.0 / 3.0) * S.bp[(Q + q) * L::A1 + r1] - T(1.0 / 3.0) * go[q] - dtv * Jg[q];
             io.f_out[q * N + c] = fn;
             io.g_out[q * N + c] = gn;
             phi += gn;
@@ -567,12 +587,12 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
         T jsum = 0, gsum = 0;
 #pragma unroll
         for (int q = 0; q < Q; q++) {
-            const T fn = T(4.0 / 3.0) * S.bp[q * L::A1 + r1] - T(1.0 / 3.0) * io.f_in[q * N + c] - dtv * Jf[q];
+            const T fn = T(4.0 / 3.0) * S.bp[q * L::A1 + r1] - T(1.0 / 3.0) * fo[q] - dtv * Jf[q];
             io.f_out[q * N + c] = fn;
             finite = finite && isfinite(fn);
             jsum += Jg[q];
             if (q > 0) {
-                const T gn = T(4.0 / 3.0) * S.bp[(Q + q) * L::A1 + r1] - T(1.0 / 3.0) * io.g_in[q * N + c] - dtv * Jg[q];
+                const T gn = T(4.0 / 3.0) * S.bp[(Q + q) * L::A1 + r1] - T(1.0 / 3.0) * go[q] - dtv * Jg[q];
                 io.g_out[q * N + c] = gn;
                 gsum += gn;
                 finite = finite && isfinite(gn);
