@@ -47,8 +47,8 @@ PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM bytes per cell of one k_step launch from the ncu capture summarised in
 # profiles/k_step_fp32_drop2048.md (dram__bytes_read.sum + dram__bytes_write.sum
 # over 4,194,304 cells), valid only for the kernel sources it was taken on.
-TRAFFIC_SOURCES_SHA = "b369c0a6d3d7c511"
-TRAFFIC_BYTES_PER_CELL_FP32 = (336.804864e6 + 297.830400e6) / 4194304
+TRAFFIC_SOURCES_SHA = "3b949e17ba0f449a"
+TRAFFIC_BYTES_PER_CELL_FP32 = (336.806400e6 + 297.182464e6) / 4194304
 
 
 def kernel_sources_sha():
