@@ -106,6 +106,36 @@ struct AxisRecT {
     int km, kp, lo_wall, hi_wall;
 };
 
+// A pair (f, g) of values of the two distribution kinds.  In FP32 the pair
+// arithmetic maps to the packed two-lane instructions of sm_100+ (one issue
+// for two FP32 FMAs), which the fused step uses wherever f and g undergo the
+// same operation; in FP64 it is two scalar operations.
+template <typename T>
+struct PairS;
+template <>
+struct PairS<float> { using type = float2; };
+template <>
+struct PairS<double> { using type = double2; };
+template <typename T>
+using pair_t = typename PairS<T>::type;
+
+__device__ __forceinline__ float2 pr(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 pr(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 pr(float a) { return make_float2(a, a); }
+__device__ __forceinline__ double2 pr(double a) { return make_double2(a, a); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 pfma(double2 a, double2 b, double2 c)
+{
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ double2 pmul(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ double2 padd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+// a - b
+__device__ __forceinline__ float2 psub(float2 a, float2 b) { return __ffma2_rn(make_float2(-1.f, -1.f), b, a); }
+__device__ __forceinline__ double2 psub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+
 // Per-instance constants.
 struct InstDev {
     int nx, ny, nxp, bcx, bcy, pad0;

@@ -86,11 +86,11 @@ struct Tile {
     T *ga;          // [11][NG] geometry coefficients, positions x -4..BX+3 then y -4..BY+3
     int *gg, *gf;   // [NG] global index (-1 outside), flags: 1 om=-1, 2 op=+1, 4 lo wall, 8 hi wall
     phi_t<T> *phi;  // R4
-    T *flux;        // [12][NFT], aliases sf and sg (dead once phase 4 ends)
+    pair_t<T> *flux;  // [6][NFT] (f, g) flux pairs, aliases sf and sg (dead once phase 4 ends)
     T *mu;          // R3
     T *p;           // R2
     T *gmx, *gmy, *lmu, *gfx, *gfy, *gpx, *gpy;  // R1
-    T *bp;          // [18][A1]: f bar-plus (0..8), g bar-plus (9..17)
+    pair_t<T> *bp;  // [9][A1]: (f, g) bar-plus pairs
     T *sf;          // tilde f on R2 [Q][A2]
     T *sg;          // tilde g on R1 [Q][A1]
     __device__ Tile(unsigned char *sm)
@@ -99,13 +99,13 @@ struct Tile {
         gg = (int *)(ga + 11 * L::NG);
         gf = gg + L::NG;
         phi = (phi_t<T> *)(sm + L::o_phi);
-        flux = (T *)(sm + L::o_un);
+        flux = (pair_t<T> *)(sm + L::o_un);
         mu = (T *)(sm + L::o_mu);
         p = (T *)(sm + L::o_p);
         T *r1 = (T *)(sm + L::o_r1);
         gmx = r1; gmy = r1 + L::A1; lmu = r1 + 2 * L::A1; gfx = r1 + 3 * L::A1; gfy = r1 + 4 * L::A1;
         gpx = r1 + 5 * L::A1; gpy = r1 + 6 * L::A1;
-        bp = r1 + 7 * L::A1;
+        bp = (pair_t<T> *)(r1 + 7 * L::A1);
         sf = (T *)(sm + L::o_f);
         sg = (T *)(sm + L::o_g);
     }
@@ -142,7 +142,7 @@ struct Tile {
 // returned as (xi . e_A) phi_i |S|.
 template <typename T, int A>
 __device__ __forceinline__ void face_tail(const InstDev &I, const T (&fb)[Q], const T (&gb)[Q], const FaceAux<T> &ax,
-                                          bool wall, int side, T area, T (&Ff)[6], T (&Fg)[6])
+                                          bool wall, int side, T area, pair_t<T> (&F2o)[6])
 {
     const ParT<T> &Pr = par<T>(I);
     const T h = Pr.h;
@@ -180,7 +180,8 @@ __device__ __forceinline__ void face_tail(const InstDev &I, const T (&fb)[Q], co
     const T r1 = fdiv(T(1), T(2) * tf + h), r2 = fdiv(T(1), T(2) * tg + h);
     const T a1 = T(2) * tf * r1, b1 = h * r1, c1 = tf * h * r1;
     const T a2 = T(2) * tg * r2, b2 = h * r2, c2 = tg * h * r2;
-    T fo[Q], go[Q];
+    const pair_t<T> ca2 = pr(a1, a2), cb2 = pr(b1, b2), cc2 = pr(c1, c2);
+    pair_t<T> o[Q];
 #pragma unroll
     for (int k = 0; k < 6; k++) {
         const int q = fset<A>(k);
@@ -188,30 +189,21 @@ __device__ __forceinline__ void face_tail(const InstDev &I, const T (&fb)[Q], co
         if (wall && ca(q, A) * side < 0) continue;
         T feq, geq, F1, F2;
         eq_src<T>(s, v, q, feq, geq, F1, F2);
-        fo[q] = a1 * fb[q] + b1 * feq + c1 * F1;
-        go[q] = a2 * gb[q] + b2 * geq + c2 * F2;
+        o[q] = pfma(ca2, pr(fb[q], gb[q]), pfma(cb2, pr(feq, geq), pmul(cc2, pr(F1, F2))));
     }
 #pragma unroll
     for (int k = 0; k < 6; k++) {
         const int q = fset<A>(k);
-        T vf, vg;
-        if (wall && ca(q, A) * side < 0) {
-            vf = fo[opp(q)];
-            vg = go[opp(q)];
-        } else {
-            vf = fo[q];
-            vg = go[q];
-        }
-        Ff[k] = T(ca(q, A)) * vf * area;
-        Fg[k] = T(ca(q, A)) * vg * area;
+        const pair_t<T> vo = (wall && ca(q, A) * side < 0) ? o[opp(q)] : o[q];
+        F2o[k] = pmul(pr(T(ca(q, A)) * area), vo);
     }
 }
 
 // Flux values of the face between positions a (low side) and b = a + e_A of a
 // tile, or of the wall face of whichever of the two lies in the domain.
 template <typename T, int BX, int BY, int A>
-__device__ __forceinline__ void tile_face(const InstDev &I, const Tile<T, BX, BY> &S, int xa, int ya, T (&Ff)[6],
-                                          T (&Fg)[6])
+__device__ __forceinline__ void tile_face(const InstDev &I, const Tile<T, BX, BY> &S, int xa, int ya,
+                                          pair_t<T> (&F2o)[6])
 {
     const ParT<T> &Pr = par<T>(I);
     using TL = Tile<T, BX, BY>;
@@ -219,7 +211,7 @@ __device__ __forceinline__ void tile_face(const InstDev &I, const Tile<T, BX, BY
     const int xb = xa + (A == 0 ? 1 : 0), yb = ya + (A == 1 ? 1 : 0);
     const int pa = A == 0 ? xa : ya, pb = A == 0 ? xb : yb, pt = A == 0 ? ya : xa;
 #pragma unroll
-    for (int k = 0; k < 6; k++) { Ff[k] = 0; Fg[k] = 0; }
+    for (int k = 0; k < 6; k++) F2o[k] = pr(T(0));
     if (S.gidx(1 - A, pt) < 0) return;
     const bool va = S.gidx(A, pa) >= 0, vb = S.gidx(A, pb) >= 0;
     const T h = Pr.h;
@@ -227,8 +219,6 @@ __device__ __forceinline__ void tile_face(const InstDev &I, const Tile<T, BX, BY
     const T te1m = S.c(4, 1 - A, pt), te10 = S.c(5, 1 - A, pt), te1p = S.c(6, 1 - A, pt);
     const int tstep = A == 0 ? TL::L::W1 : 1;
     const int tm = S.om(1 - A, pt) * tstep, tp = S.op(1 - A, pt) * tstep;
-    const T *bpf = S.bp;
-    const T *bpg = S.bp + 9 * A1;
     T fb[Q], gb[Q];
     FaceAux<T> ax;
     if (va && vb) {
@@ -236,18 +226,19 @@ __device__ __forceinline__ void tile_face(const InstDev &I, const Tile<T, BX, BY
         const T wL = S.c(7, A, pa), wR = S.c(8, A, pa), invd = S.c(9, A, pa);
 #pragma unroll
         for (int q = 0; q < Q; q++) {
-#pragma unroll
-            for (int kind = 0; kind < 2; kind++) {
-                const T *B = (kind == 0 ? bpf : bpg) + q * A1;
-                const T bL = B[ia], bR = B[ib];
-                T v = (wL * bL + wR * bR) - h * T(ca(q, A)) * ((bR - bL) * invd);
-                if (ca(q, 1 - A)) {
-                    const T tL = te1m * B[ia + tm] + te10 * bL + te1p * B[ia + tp];
-                    const T tR = te1m * B[ib + tm] + te10 * bR + te1p * B[ib + tp];
-                    v -= h * T(ca(q, 1 - A)) * (wL * tL + wR * tR);
-                }
-                (kind == 0 ? fb : gb)[q] = v;
+            // (wL bL + wR bR) - h xi_A (bR - bL) / d - h xi_t (wL tL + wR tR), for f and g at once
+            const pair_t<T> *B = S.bp + q * A1;
+            const pair_t<T> bL = B[ia], bR = B[ib];
+            const T k1 = h * T(ca(q, A)) * invd;
+            pair_t<T> v = pfma(pr(wL + k1), bL, pmul(pr(wR - k1), bR));
+            if (ca(q, 1 - A)) {
+                const pair_t<T> tL = pfma(pr(te1m), B[ia + tm], pfma(pr(te10), bL, pmul(pr(te1p), B[ia + tp])));
+                const pair_t<T> tR = pfma(pr(te1m), B[ib + tm], pfma(pr(te10), bR, pmul(pr(te1p), B[ib + tp])));
+                const T kt = -h * T(ca(q, 1 - A));
+                v = pfma(pr(kt * wL), tL, pfma(pr(kt * wR), tR, v));
             }
+            fb[q] = v.x;
+            gb[q] = v.y;
         }
         const int ma = TL::i3(xa, ya), mb = TL::i3(xb, yb);
         ax.mu = wL * S.mu[ma] + wR * S.mu[mb];
@@ -258,7 +249,7 @@ __device__ __forceinline__ void tile_face(const InstDev &I, const Tile<T, BX, BY
         ax.gphiy = wL * S.gfy[ia] + wR * S.gfy[ib];
         ax.gpx = wL * S.gpx[ia] + wR * S.gpx[ib];
         ax.gpy = wL * S.gpy[ia] + wR * S.gpy[ib];
-        face_tail<T, A>(I, fb, gb, ax, false, 0, area, Ff, Fg);
+        face_tail<T, A>(I, fb, gb, ax, false, 0, area, F2o);
         return;
     }
     int side, xc, yc, pc;
@@ -277,13 +268,13 @@ __device__ __forceinline__ void tile_face(const InstDev &I, const Tile<T, BX, BY
         if (ca(q, A) * side < 0) continue;
         const T off = T(side) * half_d - h * T(ca(q, A));
         const T ht = h * T(ca(q, 1 - A));
-#pragma unroll
-        for (int kind = 0; kind < 2; kind++) {
-            const T *B = (kind == 0 ? bpf : bpg) + q * A1;
-            const T b = B[ic];
-            (kind == 0 ? fb : gb)[q] = b + off * (ne1m * B[ic + nm] + ne10 * b + ne1p * B[ic + np])
-                                     - ht * (te1m * B[ic + tm] + te10 * b + te1p * B[ic + tp]);
-        }
+        const pair_t<T> *B = S.bp + q * A1;
+        const pair_t<T> b = B[ic];
+        const pair_t<T> dn = pfma(pr(ne1m), B[ic + nm], pfma(pr(ne10), b, pmul(pr(ne1p), B[ic + np])));
+        const pair_t<T> dtg = pfma(pr(te1m), B[ic + tm], pfma(pr(te10), b, pmul(pr(te1p), B[ic + tp])));
+        const pair_t<T> v = pfma(pr(-ht), dtg, pfma(pr(off), dn, b));
+        fb[q] = v.x;
+        gb[q] = v.y;
     }
 #pragma unroll
     for (int q = 0; q < Q; q++) {
@@ -300,7 +291,7 @@ __device__ __forceinline__ void tile_face(const InstDev &I, const Tile<T, BX, BY
     ax.gphiy = A == 1 ? T(0) : S.gfy[ic];
     ax.gpx = A == 0 ? T(0) : S.gpx[ic];
     ax.gpy = A == 1 ? T(0) : S.gpy[ic];
-    face_tail<T, A>(I, fb, gb, ax, true, side, area, Ff, Fg);
+    face_tail<T, A>(I, fb, gb, ax, true, side, area, F2o);
 }
 
 template <typename T, int BX, int BY, int MINB>
@@ -469,7 +460,7 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
         if (S.gidx(0, x) < 0 || S.gidx(1, y) < 0) {
             S.gmx[r] = 0; S.gmy[r] = 0; S.lmu[r] = 0; S.gfx[r] = 0; S.gfy[r] = 0; S.gpx[r] = 0; S.gpy[r] = 0;
 #pragma unroll
-            for (int q = 0; q < 2 * Q; q++) S.bp[q * L::A1 + r] = 0;
+            for (int q = 0; q < Q; q++) S.bp[q * L::A1 + r] = pr(T(0));
             continue;
         }
         const int k2 = TL::i2(x, y);
@@ -519,66 +510,59 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
         for (int q = 0; q < Q; q++) {
             T feq, geq, Ff, Fg;
             eq_src<T>(s, v, q, feq, geq, Ff, Fg);
-            S.bp[q * L::A1 + r] = af * fv[q] + bf * feq + cf * Ff;
-            S.bp[(Q + q) * L::A1 + r] = ag * S.sg[q * L::A1 + r] + bg * geq + cg * Fg;
+            S.bp[q * L::A1 + r] = pfma(pr(af, ag), pr(fv[q], S.sg[q * L::A1 + r]),
+                                       pfma(pr(bf, bg), pr(feq, geq), pmul(pr(cf, cg), pr(Ff, Fg))));
         }
     }
     __syncthreads();
 
-    // the tile cell's own tilde f and g for the update: loaded now so that
-    // their latency overlaps the face work
     const int x = threadIdx.x, y = threadIdx.y;
     const int gi = i0 + x, gj = j0 + y;
     const bool own = gi < I.nx && gj < I.ny;
     const long long c = own ? cell(gi, gj) : 0;
-    T fo[Q], go[Q];
-#pragma unroll
-    for (int q = 0; q < Q; q++) {
-        fo[q] = own ? io.f_in[q * N + c] : T(0);
-        go[q] = own ? io.g_in[q * N + c] : T(0);
-    }
 
     // ---- phase 5: every face of the tile once (x faces first in the index space)
     for (int k = tid; k < L::NFT; k += NT) {
-        T Ff[6], Fg[6];
-        if (k < L::NFX) tile_face<T, BX, BY, 0>(I, S, k % (BX + 1) - 1, k / (BX + 1), Ff, Fg);
-        else tile_face<T, BX, BY, 1>(I, S, (k - L::NFX) % BX, (k - L::NFX) / BX - 1, Ff, Fg);
+        pair_t<T> F2o[6];
+        if (k < L::NFX) tile_face<T, BX, BY, 0>(I, S, k % (BX + 1) - 1, k / (BX + 1), F2o);
+        else tile_face<T, BX, BY, 1>(I, S, (k - L::NFX) % BX, (k - L::NFX) / BX - 1, F2o);
 #pragma unroll
-        for (int m = 0; m < 6; m++) { S.flux[m * L::NFT + k] = Ff[m]; S.flux[(6 + m) * L::NFT + k] = Fg[m]; }
+        for (int m = 0; m < 6; m++) S.flux[m * L::NFT + k] = F2o[m];
     }
     __syncthreads();
 
     // ---- phase 6: update of the tile cell (Eqs. relations2, updatef)
     if (!own) return;
-    T Jf[Q], Jg[Q];
-    Jf[0] = 0; Jg[0] = 0;
+    // J of both kinds at once: east minus west for the x set, north minus south for the y set
+    pair_t<T> J[Q];
+#pragma unroll
+    for (int q = 0; q < Q; q++) J[q] = pr(T(0));
     {
         const int kw = y * (BX + 1) + x, ke = kw + 1;                 // west and east faces
         const int ks = L::NFX + y * BX + x, kn = ks + BX;            // south and north faces
 #pragma unroll
-        for (int q = 1; q < Q; q++) { Jf[q] = 0; Jg[q] = 0; }
-#pragma unroll
         for (int m = 0; m < 6; m++) {
             const int qx = xset(m), qy = yset(m);
-            Jf[qx] += S.flux[m * L::NFT + ke] - S.flux[m * L::NFT + kw];
-            Jg[qx] += S.flux[(6 + m) * L::NFT + ke] - S.flux[(6 + m) * L::NFT + kw];
-            Jf[qy] += S.flux[m * L::NFT + kn] - S.flux[m * L::NFT + ks];
-            Jg[qy] += S.flux[(6 + m) * L::NFT + kn] - S.flux[(6 + m) * L::NFT + ks];
+            J[qx] = padd(J[qx], psub(S.flux[m * L::NFT + ke], S.flux[m * L::NFT + kw]));
+            J[qy] = padd(J[qy], psub(S.flux[m * L::NFT + kn], S.flux[m * L::NFT + ks]));
         }
     }
     const int r1 = TL::i1(x, y);
     const T dtv = dt / (S.c(10, 0, x) * S.c(10, 1, y));
+    // tilde^{n+1} = 4/3 bar-plus - 1/3 tilde - dt/|V| J
+    pair_t<T> nw[Q];
+#pragma unroll
+    for (int q = 0; q < Q; q++)
+        nw[q] = pfma(pr(T(4.0 / 3.0)), S.bp[q * L::A1 + r1], pfma(pr(T(-1.0 / 3.0)), pr(io.f_in[q * N + c], io.g_in[q * N + c]), pmul(pr(-dtv), J[q])));
     bool finite = true;
     if constexpr (sizeof(T) == sizeof(double)) {
         T phi = 0;
 #pragma unroll
         for (int q = 0; q < Q; q++) {
-            const T fn = T(4.0 / 3.0) * S.bp[q * L::A1 + r1] - T(1.0 / 3.0) * fo[q] - dtv * Jf[q];
-            const T gn = T(4.0 / 3.0) * S.bp[(Q + q) * L::A1 + r1] - T(1.0 / 3.0) * go[q] - dtv * Jg[q];
-            io.f_out[q * N + c] = fn;
-            io.g_out[q * N + c] = gn;
-            phi += gn;
-            finite = finite && isfinite(fn) && isfinite(gn);
+            io.f_out[q * N + c] = nw[q].x;
+            io.g_out[q * N + c] = nw[q].y;
+            phi += nw[q].y;
+            finite = finite && isfinite(nw[q].x) && isfinite(nw[q].y);
         }
         io.phi_out[c] = phi;
     } else {
@@ -587,15 +571,13 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
         T jsum = 0, gsum = 0;
 #pragma unroll
         for (int q = 0; q < Q; q++) {
-            const T fn = T(4.0 / 3.0) * S.bp[q * L::A1 + r1] - T(1.0 / 3.0) * fo[q] - dtv * Jf[q];
-            io.f_out[q * N + c] = fn;
-            finite = finite && isfinite(fn);
-            jsum += Jg[q];
+            io.f_out[q * N + c] = nw[q].x;
+            finite = finite && isfinite(nw[q].x);
+            jsum += J[q].y;
             if (q > 0) {
-                const T gn = T(4.0 / 3.0) * S.bp[(Q + q) * L::A1 + r1] - T(1.0 / 3.0) * go[q] - dtv * Jg[q];
-                io.g_out[q * N + c] = gn;
-                gsum += gn;
-                finite = finite && isfinite(gn);
+                io.g_out[q * N + c] = nw[q].y;
+                gsum += nw[q].y;
+                finite = finite && isfinite(nw[q].y);
             }
         }
         const phi_t<T> phi = phi_add(io.phi_in[c], -(dtv * jsum));   // an L2 hit: read in phase 1
