@@ -167,6 +167,15 @@ int dugks_set_tile_shape(dugks_sim *sim, int shape);
 int dugks_tile_shape(const dugks_sim *sim, int *shape, int *bx, int *by);
 const char *dugks_tile_shape_name(int shape);
 
+/* Number of instances that take the fused step's uniform periodic path: both
+   axes periodic and every spacing of an axis equal (bit for bit).  Their
+   geometry is one record per axis, so that path skips the per-position
+   geometry reads and the wall branches; its results equal the general path's
+   bit for bit.  A batch holding both kinds launches one kernel per kind each
+   step.  Setting DUGKS_GENERAL_ONLY=1 in the environment before creation sends
+   every instance through the general path. */
+int dugks_uniform_instances(const dugks_sim *sim, int *n);
+
 const char *dugks_status_str(int status);
 
 /* Allocation-free FP64 conservation sums of one mesh.  The paper has no

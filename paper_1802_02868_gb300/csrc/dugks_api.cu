@@ -53,9 +53,13 @@ struct dugks_sim {
     double *d_phi_alt = nullptr;
     bool fused = true;            // one-launch step (k_step) or the four-kernel step
     bool use_graph = true;        // replay multi-step calls from a captured two-step graph
+    bool use_uni = true;          // uniform periodic instances take the specialised fused step
     int shape = 0;                // tile shape of the fused step (index into kShapes)
+    // fused-step tile tables per shape: the tiles of uniform periodic instances
+    // first (n_uni_s of them), then the rest
     int4 *d_tiles_s[DUGKS_NUM_TILE_SHAPES] = {};
     int n_tiles_s[DUGKS_NUM_TILE_SHAPES] = {};
+    int n_uni_s[DUGKS_NUM_TILE_SHAPES] = {};
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph2 = nullptr;   // k_step(A -> B), k_step(B -> A)
     int *d_status = nullptr;
@@ -180,14 +184,16 @@ cudaEvent_t take_event(dugks_sim *s)
 }
 
 // Bracket one launch with events when timing is on.
+// Events around `count` passes of kernel k (k < 0: counted, not timed), which
+// launch `launches` kernels in all (default: one per pass).
 struct Timed {
     dugks_sim *s;
     int k;
     int count;
     cudaEvent_t a = nullptr, b = nullptr;
-    Timed(dugks_sim *s_, int k_, int count_ = 1) : s(s_), k(k_), count(count_)
+    Timed(dugks_sim *s_, int k_, int count_ = 1, int launches_ = -1) : s(s_), k(k_), count(count_)
     {
-        s->launches += count;
+        s->launches += launches_ < 0 ? count : launches_;
         if (s->timing && k >= 0) {
             a = take_event(s);
             b = take_event(s);
@@ -228,29 +234,31 @@ int prepare_shape()
     using L = FusedLayout<T, BX, BY>;
     static bool attr_set = false;   // per instantiation; set before the first launch
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_step<T, BX, BY, fused_minb<T, BX, BY>()>,
+        cudaError_t e = cudaFuncSetAttribute(k_step<T, BX, BY, fused_minb<T, BX, BY>(), false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_step<T, BX, BY, fused_minb<T, BX, BY>(), true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
         if (e != cudaSuccess) return cuda_status(e);
         attr_set = true;
     }
     return DUGKS_OK;
 }
 
-// tile table of shape k (shape 0 is the table every other kernel uses)
+// fused-step tile table of shape k: the uniform periodic instances' tiles first
 int ensure_tiles(dugks_sim *s, int k)
 {
-    if (k == 0) {
-        s->d_tiles_s[0] = s->d_tiles;
-        s->n_tiles_s[0] = s->n_tiles;
-        return DUGKS_OK;
-    }
     if (s->d_tiles_s[k]) return DUGKS_OK;
     std::vector<int4> tiles;
     const int bx = kShapes[k].bx, by = kShapes[k].by;
-    for (int i = 0; i < s->n_inst; i++) {
-        const InstDev &I = s->h_inst[i];
-        for (int ty = 0; ty < I.ny; ty += by)
-            for (int tx = 0; tx < I.nx; tx += bx) tiles.push_back(make_int4(i, tx, ty, 0));
+    for (int pass = 0; pass < 2; pass++) {
+        for (int i = 0; i < s->n_inst; i++) {
+            const InstDev &I = s->h_inst[i];
+            if ((pass == 0) != (s->use_uni && I.uni)) continue;
+            for (int ty = 0; ty < I.ny; ty += by)
+                for (int tx = 0; tx < I.nx; tx += bx) tiles.push_back(make_int4(i, tx, ty, 0));
+        }
+        if (pass == 0) s->n_uni_s[k] = (int)tiles.size();
     }
     cudaError_t e = cudaMalloc(&s->d_tiles_s[k], sizeof(int4) * tiles.size());
     if (e == cudaSuccess) e = cudaMemcpy(s->d_tiles_s[k], tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice);
@@ -289,12 +297,22 @@ StepIO<T> step_io(dugks_sim *s)
     return io;
 }
 
+// kernels one fused step launches: one per class of instance present
+int fused_launches(const dugks_sim *s)
+{
+    const int k = s->shape;
+    return (s->n_uni_s[k] > 0) + (s->n_tiles_s[k] > s->n_uni_s[k]);
+}
+
 template <typename T, int BX, int BY>
 void enqueue_shape(dugks_sim *s, int k, const StepIO<T> &io, cudaStream_t st)
 {
     using L = FusedLayout<T, BX, BY>;
-    k_step<T, BX, BY, fused_minb<T, BX, BY>()><<<(unsigned)s->n_tiles_s[k], dim3(BX, BY), L::bytes, st>>>(
-        s->d_inst, s->d_tiles_s[k], (const AxisRecT<T> *)s->d_geoT, io);
+    constexpr int MB = fused_minb<T, BX, BY>();
+    const int nu = s->n_uni_s[k], ng = s->n_tiles_s[k] - nu;
+    const AxisRecT<T> *geo = (const AxisRecT<T> *)s->d_geoT;
+    if (nu > 0) k_step<T, BX, BY, MB, true><<<(unsigned)nu, dim3(BX, BY), L::bytes, st>>>(s->d_inst, s->d_tiles_s[k], geo, io);
+    if (ng > 0) k_step<T, BX, BY, MB, false><<<(unsigned)ng, dim3(BX, BY), L::bytes, st>>>(s->d_inst, s->d_tiles_s[k] + nu, geo, io);
 }
 
 template <typename T>
@@ -323,7 +341,7 @@ int launch_fused(dugks_sim *s)
     int rc = prepare_fused<T>(s);
     if (rc) return rc;
     const StepIO<T> io = step_io<T>(s);
-    { Timed t(s, K_STEP); enqueue_fused<T>(s, io, s->stream); }
+    { Timed t(s, K_STEP, 1, fused_launches(s)); enqueue_fused<T>(s, io, s->stream); }
     swap_state<T>(s, io);
     return cuda_status(cudaGetLastError());
 }
@@ -371,7 +389,7 @@ int step_fused(dugks_sim *s, long n)
             if (rc) return rc;
         }
         for (; k + 2 <= n; k += 2) {
-            Timed t(s, K_STEP, 2);
+            Timed t(s, K_STEP, 2, 2 * fused_launches(s));
             cudaError_t e = cudaGraphLaunch(s->graph2, s->stream);
             if (e != cudaSuccess) return cuda_status(e);
         }
@@ -500,7 +518,7 @@ void free_sim(dugks_sim *s)
     if (!s) return;
     cudaFree(s->d_inst);
     cudaFree(s->d_tiles);
-    for (int k = 1; k < DUGKS_NUM_TILE_SHAPES; k++) cudaFree(s->d_tiles_s[k]);
+    for (int k = 0; k < DUGKS_NUM_TILE_SHAPES; k++) cudaFree(s->d_tiles_s[k]);
     cudaFree(s->d_geo);
     cudaFree(s->d_geoT);
     cudaFree(s->d_dense0);
@@ -727,6 +745,8 @@ int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *para
         s->fused = !(env && env[0] == '1');
         const char *g = std::getenv("DUGKS_NO_GRAPH");
         s->use_graph = !(g && g[0] == '1');
+        const char *u = std::getenv("DUGKS_GENERAL_ONLY");
+        s->use_uni = !(u && u[0] == '1');
     }
     s->stream = (cudaStream_t)cuda_stream;
     std::vector<AxisRec> geo;
@@ -742,6 +762,9 @@ int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *para
         I.nxp = (m.nx + 31) / 32 * 32;
         I.bcx = m.bc_x;
         I.bcy = m.bc_y;
+        I.uni = m.bc_x == DUGKS_BC_PERIODIC && m.bc_y == DUGKS_BC_PERIODIC;
+        for (int i = 1; i < m.nx && I.uni; i++) I.uni = m.dx[i] == m.dx[0];
+        for (int j = 1; j < m.ny && I.uni; j++) I.uni = m.dy[j] == m.dy[0];
         I.cell0 = cell;
         cell += (long long)I.nxp * m.ny;
         s->h_dense0.push_back(dense);
@@ -1127,6 +1150,15 @@ int dugks_autotune(dugks_sim *s, int steps, int *chosen, double *ms_per_step)
         if (ms_per_step) *ms_per_step = best_ms / steps;
     }
     return rc;
+}
+
+int dugks_uniform_instances(const dugks_sim *s, int *n)
+{
+    if (!s || !n) return DUGKS_ERR_ARG;
+    int k = 0;
+    for (const InstDev &I : s->h_inst) k += (s->use_uni && I.uni) ? 1 : 0;
+    *n = k;
+    return DUGKS_OK;
 }
 
 const char *dugks_tile_shape_name(int shape)

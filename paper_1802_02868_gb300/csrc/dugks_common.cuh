@@ -138,7 +138,8 @@ __device__ __forceinline__ double2 psub(double2 a, double2 b) { return make_doub
 
 // Per-instance constants.
 struct InstDev {
-    int nx, ny, nxp, bcx, bcy, pad0;
+    int nx, ny, nxp, bcx, bcy;
+    int uni;           // uniform spacing on both axes, both periodic
     long long cell0;   // first cell of the instance in the batch cell space
     long long gx_off;  // index of the x-axis records in the geometry table
     long long gy_off;

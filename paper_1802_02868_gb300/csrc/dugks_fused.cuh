@@ -79,8 +79,13 @@ struct G1 {
     int g, om, op, lo, hi;
 };
 
-// Shared-memory views of one CTA.
-template <typename T, int BX, int BY>
+// Shared-memory views of one CTA.  UNI marks an instance whose spacing is
+// uniform on each axis and whose axes are both periodic: every position then
+// has the same geometry record (the records depend only on the spacings of a
+// cell and its two neighbours), every neighbour exists, and there are no wall
+// faces, so the accessors below return the record of position 0 and constant
+// neighbour offsets.  The arithmetic is that of the general path, bit for bit.
+template <typename T, int BX, int BY, bool UNI = false>
 struct Tile {
     using L = FusedLayout<T, BX, BY>;
     T *ga;          // [11][NG] geometry coefficients, positions x -4..BX+3 then y -4..BY+3
@@ -116,6 +121,8 @@ struct Tile {
     // entry of x position x (axis 0) or y position y (axis 1)
     static __device__ __forceinline__ int ge(int axis, int pos) { return axis == 0 ? pos + 4 : L::W4 + pos + 4; }
     __device__ __forceinline__ int gidx(int axis, int pos) const { return gg[ge(axis, pos)]; }
+    // position inside the domain (always, on a periodic axis)
+    __device__ __forceinline__ bool ok(int axis, int pos) const { return UNI || gg[ge(axis, pos)] >= 0; }
     __device__ __forceinline__ G1<T> geo(int axis, int pos) const
     {
         const int e = ge(axis, pos);
@@ -131,9 +138,9 @@ struct Tile {
         G.hi = (f >> 3) & 1;
         return G;
     }
-    __device__ __forceinline__ int om(int axis, int pos) const { return (gf[ge(axis, pos)] & 1) ? -1 : 0; }
-    __device__ __forceinline__ int op(int axis, int pos) const { return (gf[ge(axis, pos)] & 2) ? 1 : 0; }
-    __device__ __forceinline__ T c(int k, int axis, int pos) const { return ga[k * L::NG + ge(axis, pos)]; }
+    __device__ __forceinline__ int om(int axis, int pos) const { return UNI ? -1 : (gf[ge(axis, pos)] & 1) ? -1 : 0; }
+    __device__ __forceinline__ int op(int axis, int pos) const { return UNI ? 1 : (gf[ge(axis, pos)] & 2) ? 1 : 0; }
+    __device__ __forceinline__ T c(int k, int axis, int pos) const { return ga[k * L::NG + ge(axis, UNI ? 0 : pos)]; }
 };
 
 // Face macroscopic variables from the nine bar distributions of each kind at
@@ -201,19 +208,19 @@ __device__ __forceinline__ void face_tail(const InstDev &I, const T (&fb)[Q], co
 
 // Flux values of the face between positions a (low side) and b = a + e_A of a
 // tile, or of the wall face of whichever of the two lies in the domain.
-template <typename T, int BX, int BY, int A>
-__device__ __forceinline__ void tile_face(const InstDev &I, const Tile<T, BX, BY> &S, int xa, int ya,
+template <typename T, int BX, int BY, int A, bool UNI>
+__device__ __forceinline__ void tile_face(const InstDev &I, const Tile<T, BX, BY, UNI> &S, int xa, int ya,
                                           pair_t<T> (&F2o)[6])
 {
     const ParT<T> &Pr = par<T>(I);
-    using TL = Tile<T, BX, BY>;
+    using TL = Tile<T, BX, BY, UNI>;
     constexpr int A1 = TL::L::A1;
     const int xb = xa + (A == 0 ? 1 : 0), yb = ya + (A == 1 ? 1 : 0);
     const int pa = A == 0 ? xa : ya, pb = A == 0 ? xb : yb, pt = A == 0 ? ya : xa;
 #pragma unroll
     for (int k = 0; k < 6; k++) F2o[k] = pr(T(0));
-    if (S.gidx(1 - A, pt) < 0) return;
-    const bool va = S.gidx(A, pa) >= 0, vb = S.gidx(A, pb) >= 0;
+    if (!S.ok(1 - A, pt)) return;
+    const bool va = S.ok(A, pa), vb = S.ok(A, pb);
     const T h = Pr.h;
     const T area = S.c(10, 1 - A, pt);
     const T te1m = S.c(4, 1 - A, pt), te10 = S.c(5, 1 - A, pt), te1p = S.c(6, 1 - A, pt);
@@ -221,7 +228,7 @@ __device__ __forceinline__ void tile_face(const InstDev &I, const Tile<T, BX, BY
     const int tm = S.om(1 - A, pt) * tstep, tp = S.op(1 - A, pt) * tstep;
     T fb[Q], gb[Q];
     FaceAux<T> ax;
-    if (va && vb) {
+    if (UNI || (va && vb)) {
         const int ia = TL::i1(xa, ya), ib = TL::i1(xb, yb);
         const T wL = S.c(7, A, pa), wR = S.c(8, A, pa), invd = S.c(9, A, pa);
 #pragma unroll
@@ -294,11 +301,11 @@ __device__ __forceinline__ void tile_face(const InstDev &I, const Tile<T, BX, BY
     face_tail<T, A>(I, fb, gb, ax, true, side, area, F2o);
 }
 
-template <typename T, int BX, int BY, int MINB>
+template <typename T, int BX, int BY, int MINB, bool UNI>
 __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles,
                                                        const AxisRecT<T> *__restrict__ geo, StepIO<T> io)
 {
-    using TL = Tile<T, BX, BY>;
+    using TL = Tile<T, BX, BY, UNI>;
     using L = typename TL::L;
     extern __shared__ __align__(16) unsigned char smem[];
     TL S(smem);
@@ -334,7 +341,7 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
     // issued first so that their latency overlaps the geometry set-up.
     for (int r = tid; r < L::A4; r += NT) {
         const int gi = gpos(true, r % L::W4 - 4), gj = gpos(false, r / L::W4 - 4);
-        if (gi >= 0 && gj >= 0) {
+        if (UNI || (gi >= 0 && gj >= 0)) {
             cp_async<sizeof(phi_t<T>)>(S.phi + r, io.phi_in + cell(gi, gj));
         } else {
             phi_t<T> v;
@@ -345,7 +352,7 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
     cp_commit();
     for (int r = tid; r < L::A2; r += NT) {
         const int gi = gpos(true, r % L::W2 - 2), gj = gpos(false, r / L::W2 - 2);
-        if (gi >= 0 && gj >= 0) {
+        if (UNI || (gi >= 0 && gj >= 0)) {
             const long long c = cell(gi, gj);
 #pragma unroll
             for (int q = 0; q < Q; q++) cp_async<sizeof(T)>(S.sf + q * L::A2 + r, io.f_in + q * N + c);
@@ -356,7 +363,7 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
     }
     for (int r = tid; r < L::A1; r += NT) {
         const int gi = gpos(true, r % L::W1 - 1), gj = gpos(false, r / L::W1 - 1);
-        if (gi >= 0 && gj >= 0) {
+        if (UNI || (gi >= 0 && gj >= 0)) {
             const long long c = cell(gi, gj);
 #pragma unroll
             for (int q = 0; q < Q; q++) cp_async<sizeof(T)>(S.sg + q * L::A1 + r, io.g_in + q * N + c);
@@ -372,7 +379,7 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
         const bool isx = r < L::W4;
         const int pos = isx ? r - 4 : r - L::W4 - 4;
         const int g = S.gg[r];
-        (void)pos;
+        if (UNI && pos != 0) continue;   // every position carries the record of position 0
         T v[11];
         int fl = 0;
         if (g >= 0) {
@@ -396,7 +403,7 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
     for (int r = tid; r < L::A3; r += NT) {
         const int x = r % L::W3 - 3, y = r / L::W3 - 3;
         T mu = 0;
-        if (S.gidx(0, x) >= 0 && S.gidx(1, y) >= 0) {
+        if (S.ok(0, x) && S.ok(1, y)) {
             const phi_t<T> p0 = S.phi[TL::i4(x, y)];
             const T lap = (S.c(2, 0, x) * phi_sub(S.phi[TL::i4(x + S.om(0, x), y)], p0)
                          + S.c(3, 0, x) * phi_sub(S.phi[TL::i4(x + S.op(0, x), y)], p0))
@@ -418,7 +425,7 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
     for (int r = tid; r < L::A2; r += NT) {
         const int x = r % L::W2 - 2, y = r / L::W2 - 2;
         T vp = 0;
-        if (S.gidx(0, x) >= 0 && S.gidx(1, y) >= 0) {
+        if (S.ok(0, x) && S.ok(1, y)) {
             const T m0 = S.mu[TL::i3(x, y)];
             const T mxm = S.mu[TL::i3(x + S.om(0, x), y)] - m0, mxp = S.mu[TL::i3(x + S.op(0, x), y)] - m0;
             const T mym = S.mu[TL::i3(x, y + S.om(1, y))] - m0, myp = S.mu[TL::i3(x, y + S.op(1, y))] - m0;
@@ -457,7 +464,7 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
     const T ag = (T(2) * tg - h) * rg, bg = T(3) * h * rg, cg = T(3) * tg * h * rg;
     for (int r = tid; r < L::A1; r += NT) {
         const int x = r % L::W1 - 1, y = r / L::W1 - 1;
-        if (S.gidx(0, x) < 0 || S.gidx(1, y) < 0) {
+        if (!S.ok(0, x) || !S.ok(1, y)) {
             S.gmx[r] = 0; S.gmy[r] = 0; S.lmu[r] = 0; S.gfx[r] = 0; S.gfy[r] = 0; S.gpx[r] = 0; S.gpy[r] = 0;
 #pragma unroll
             for (int q = 0; q < Q; q++) S.bp[q * L::A1 + r] = pr(T(0));
@@ -524,8 +531,8 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
     // ---- phase 5: every face of the tile once (x faces first in the index space)
     for (int k = tid; k < L::NFT; k += NT) {
         pair_t<T> F2o[6];
-        if (k < L::NFX) tile_face<T, BX, BY, 0>(I, S, k % (BX + 1) - 1, k / (BX + 1), F2o);
-        else tile_face<T, BX, BY, 1>(I, S, (k - L::NFX) % BX, (k - L::NFX) / BX - 1, F2o);
+        if (k < L::NFX) tile_face<T, BX, BY, 0, UNI>(I, S, k % (BX + 1) - 1, k / (BX + 1), F2o);
+        else tile_face<T, BX, BY, 1, UNI>(I, S, (k - L::NFX) % BX, (k - L::NFX) / BX - 1, F2o);
 #pragma unroll
         for (int m = 0; m < 6; m++) S.flux[m * L::NFT + k] = F2o[m];
     }

@@ -53,7 +53,7 @@ EXPORTS = ("dugks_create", "dugks_batch_create", "dugks_destroy", "dugks_init", 
            "dugks_launch_count", "dugks_set_timing", "dugks_kernel_times", "dugks_kernel_name",
            "dugks_kernel_bytes_per_cell", "dugks_status_str", "dugks_conservation_static",
            "dugks_autotune", "dugks_set_tile_shape", "dugks_tile_shape", "dugks_tile_shape_name",
-           "dugks_adjoint")
+           "dugks_adjoint", "dugks_uniform_instances")
 STATIC_MAX_CELLS = 16777216
 
 
@@ -97,6 +97,7 @@ def load(build_if_missing: bool = True):
     L.dugks_autotune.argtypes = [vp, ip, ctypes.POINTER(ctypes.c_int), dp]
     L.dugks_set_tile_shape.argtypes = [vp, ip]
     L.dugks_tile_shape.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int)] * 3
+    L.dugks_uniform_instances.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.dugks_tile_shape_name.argtypes = [ip]
     L.dugks_tile_shape_name.restype = ctypes.c_char_p
     L.dugks_status_str.argtypes = [ip]
@@ -242,6 +243,12 @@ class Sim:
         if buf.shape[2] != self.ncells:
             raise ValueError("state has %d cells, expected %d" % (buf.shape[2], self.ncells))
         _check("dugks_load", load().dugks_load(self.h, buf.ctypes.data_as(ctypes.c_void_p), buf.nbytes))
+
+    def uniform_instances(self):
+        """Instances on the fused step's uniform periodic path."""
+        v = ctypes.c_int()
+        _check("dugks_uniform_instances", load().dugks_uniform_instances(self.h, ctypes.byref(v)))
+        return v.value
 
     def launch_count(self):
         v = ctypes.c_long()

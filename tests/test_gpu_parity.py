@@ -219,3 +219,36 @@ def test_tile_shapes_agree_and_autotune_restores_state(prec):
     f, g = s.state()
     f1, g1 = sims[1].state()
     assert normwise(f, f1) < tol and normwise(g, g1) < tol
+
+
+@pytest.mark.parametrize("prec", [dugks.FP64, dugks.FP32])
+def test_uniform_periodic_path_equals_general_path(prec, monkeypatch):
+    """The fused step's uniform periodic specialisation reproduces the general
+    path bit for bit, and a batch holding both kinds launches one kernel per
+    kind each step."""
+    cases = [CASES[0][1], CASES[1][1], CASES[2][1], I.roofline_drop(96)]
+    kinds = []
+    states = []
+    for general in ("1", "0"):
+        monkeypatch.setenv("DUGKS_GENERAL_ONLY", general)
+        s = dugks.Sim([c.mesh for c in cases], [c.params for c in cases], prec)
+        monkeypatch.delenv("DUGKS_GENERAL_ONLY")
+        kinds.append(s.uniform_instances())
+        s.init([c.phi0 for c in cases])
+        l0 = s.launch_count()
+        s.step(1)
+        l1 = s.launch_count()
+        s.step(12)
+        l2 = s.launch_count()
+        states.append(s.state())
+        if general == "0":
+            assert l1 - l0 == 2 and l2 - l1 == 24
+        else:
+            assert l1 - l0 == 1 and l2 - l1 == 12
+        s.close()
+    # the periodic uniform drops take the specialised path; the stretched
+    # channel and the walled RT box do not
+    assert kinds == [0, 2]
+    for a, b in zip(states[0], states[1]):
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y)
