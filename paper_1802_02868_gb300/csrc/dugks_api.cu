@@ -80,12 +80,18 @@ struct dugks_sim {
 
 namespace {
 
-// Tile shapes of the fused step that the autotuner chooses from.
+// Tile shapes of the fused step that the autotuner chooses from: a BX x BY
+// tile per thread block of NT threads; "sep" gives the face fluxes their own
+// shared memory (two blocks per SM instead of three in FP32).
 struct ShapeDesc {
-    int bx, by;
+    int bx, by, nt, sep;
     const char *name;
 };
-const ShapeDesc kShapes[DUGKS_NUM_TILE_SHAPES] = {{32, 8, "32x8"}, {16, 16, "16x16"}, {32, 12, "32x12"}};
+const ShapeDesc kShapes[DUGKS_NUM_TILE_SHAPES] = {{32, 8, 256, 0, "32x8"},
+                                                  {16, 16, 256, 0, "16x16"},
+                                                  {32, 12, 384, 0, "32x12"},
+                                                  {32, 8, 352, 1, "32x8/352 sep"},
+                                                  {32, 8, 384, 1, "32x8/384 sep"}};
 
 const char *kNames[K_COUNT] = {"k_mu", "k_macro", "k_cell", "k_face", "k_init", "k_reduce", "k_step"};
 
@@ -225,19 +231,20 @@ void harvest_events(dugks_sim *s)
 
 // Resident CTAs per SM that the registers of a fused-step instantiation are
 // sized for (shared memory allows the same count).
-template <typename T, int BX, int BY>
-constexpr int fused_minb() { return sizeof(T) == 8 ? 1 : (BX * BY > 256 ? 2 : 3); }
+template <typename T, int NT, bool SEP>
+constexpr int fused_minb() { return sizeof(T) == 8 ? 1 : (SEP || NT > 256 ? 2 : 3); }
 
-template <typename T, int BX, int BY>
+template <typename T, int BX, int BY, int NT, bool SEP>
 int prepare_shape()
 {
-    using L = FusedLayout<T, BX, BY>;
+    using L = FusedLayout<T, BX, BY, SEP>;
+    constexpr int MB = fused_minb<T, NT, SEP>();
     static bool attr_set = false;   // per instantiation; set before the first launch
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_step<T, BX, BY, fused_minb<T, BX, BY>(), false>,
+        cudaError_t e = cudaFuncSetAttribute(k_step<T, BX, BY, NT, MB, false, SEP>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_step<T, BX, BY, fused_minb<T, BX, BY>(), true>,
+            e = cudaFuncSetAttribute(k_step<T, BX, BY, NT, MB, true, SEP>,
                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
         if (e != cudaSuccess) return cuda_status(e);
         attr_set = true;
@@ -277,9 +284,11 @@ int prepare_fused(dugks_sim *s)
     int rc = ensure_tiles(s, s->shape);
     if (rc) return rc;
     switch (s->shape) {
-    case 1: return prepare_shape<T, 16, 16>();
-    case 2: return prepare_shape<T, 32, 12>();
-    default: return prepare_shape<T, 32, 8>();
+    case 1: return prepare_shape<T, 16, 16, 256, false>();
+    case 2: return prepare_shape<T, 32, 12, 384, false>();
+    case 3: return prepare_shape<T, 32, 8, 352, true>();
+    case 4: return prepare_shape<T, 32, 8, 384, true>();
+    default: return prepare_shape<T, 32, 8, 256, false>();
     }
 }
 
@@ -304,24 +313,26 @@ int fused_launches(const dugks_sim *s)
     return (s->n_uni_s[k] > 0) + (s->n_tiles_s[k] > s->n_uni_s[k]);
 }
 
-template <typename T, int BX, int BY>
+template <typename T, int BX, int BY, int NT, bool SEP>
 void enqueue_shape(dugks_sim *s, int k, const StepIO<T> &io, cudaStream_t st)
 {
-    using L = FusedLayout<T, BX, BY>;
-    constexpr int MB = fused_minb<T, BX, BY>();
+    using L = FusedLayout<T, BX, BY, SEP>;
+    constexpr int MB = fused_minb<T, NT, SEP>();
     const int nu = s->n_uni_s[k], ng = s->n_tiles_s[k] - nu;
     const AxisRecT<T> *geo = (const AxisRecT<T> *)s->d_geoT;
-    if (nu > 0) k_step<T, BX, BY, MB, true><<<(unsigned)nu, dim3(BX, BY), L::bytes, st>>>(s->d_inst, s->d_tiles_s[k], geo, io);
-    if (ng > 0) k_step<T, BX, BY, MB, false><<<(unsigned)ng, dim3(BX, BY), L::bytes, st>>>(s->d_inst, s->d_tiles_s[k] + nu, geo, io);
+    if (nu > 0) k_step<T, BX, BY, NT, MB, true, SEP><<<(unsigned)nu, NT, L::bytes, st>>>(s->d_inst, s->d_tiles_s[k], geo, io);
+    if (ng > 0) k_step<T, BX, BY, NT, MB, false, SEP><<<(unsigned)ng, NT, L::bytes, st>>>(s->d_inst, s->d_tiles_s[k] + nu, geo, io);
 }
 
 template <typename T>
 void enqueue_fused(dugks_sim *s, const StepIO<T> &io, cudaStream_t st)
 {
     switch (s->shape) {
-    case 1: enqueue_shape<T, 16, 16>(s, 1, io, st); break;
-    case 2: enqueue_shape<T, 32, 12>(s, 2, io, st); break;
-    default: enqueue_shape<T, 32, 8>(s, 0, io, st); break;
+    case 1: enqueue_shape<T, 16, 16, 256, false>(s, 1, io, st); break;
+    case 2: enqueue_shape<T, 32, 12, 384, false>(s, 2, io, st); break;
+    case 3: enqueue_shape<T, 32, 8, 352, true>(s, 3, io, st); break;
+    case 4: enqueue_shape<T, 32, 8, 384, true>(s, 4, io, st); break;
+    default: enqueue_shape<T, 32, 8, 256, false>(s, 0, io, st); break;
     }
 }
 

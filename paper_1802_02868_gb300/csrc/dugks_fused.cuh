@@ -30,7 +30,7 @@ struct StepIO {
     int *status;
 };
 
-template <typename T, int BX, int BY>
+template <typename T, int BX, int BY, bool SEP = false>
 struct FusedLayout {
     static constexpr int W1 = BX + 2, H1 = BY + 2, A1 = W1 * H1;
     static constexpr int W2 = BX + 4, H2 = BY + 4, A2 = W2 * H2;
@@ -46,13 +46,15 @@ struct FusedLayout {
     static constexpr size_t o_p = al(o_mu + sizeof(T) * A3);
     static constexpr size_t o_r1 = al(o_p + sizeof(T) * A2);
     // tilde f on R2 and tilde g on R1 (phases 1-4); the face fluxes (phase
-    // 5-6) reuse the same bytes once the bar-plus phase is done
+    // 5-6) reuse the same bytes once the bar-plus phase is done, unless SEP
+    // gives them their own (then the update reads its tilde values here)
     static constexpr size_t o_un = al(o_r1 + sizeof(T) * NR1 * A1);
     static constexpr size_t un_fg = sizeof(T) * Q * (A2 + A1);
     static constexpr size_t un_flux = sizeof(T) * 12 * NFT;
     static constexpr size_t o_f = o_un;
     static constexpr size_t o_g = o_un + sizeof(T) * Q * A2;
-    static constexpr size_t bytes = al(o_un + (un_fg > un_flux ? un_fg : un_flux));
+    static constexpr size_t o_flux = SEP ? al(o_un + un_fg) : o_un;
+    static constexpr size_t bytes = SEP ? al(o_flux + un_flux) : al(o_un + (un_fg > un_flux ? un_fg : un_flux));
 };
 
 // Asynchronous global -> shared copies (cp.async), grouped and awaited.
@@ -85,13 +87,13 @@ struct G1 {
 // cell and its two neighbours), every neighbour exists, and there are no wall
 // faces, so the accessors below return the record of position 0 and constant
 // neighbour offsets.  The arithmetic is that of the general path, bit for bit.
-template <typename T, int BX, int BY, bool UNI = false>
+template <typename T, int BX, int BY, bool UNI = false, bool SEP = false>
 struct Tile {
-    using L = FusedLayout<T, BX, BY>;
+    using L = FusedLayout<T, BX, BY, SEP>;
     T *ga;          // [11][NG] geometry coefficients, positions x -4..BX+3 then y -4..BY+3
     int *gg, *gf;   // [NG] global index (-1 outside), flags: 1 om=-1, 2 op=+1, 4 lo wall, 8 hi wall
     phi_t<T> *phi;  // R4
-    pair_t<T> *flux;  // [6][NFT] (f, g) flux pairs, aliases sf and sg (dead once phase 4 ends)
+    pair_t<T> *flux;  // [6][NFT] (f, g) flux pairs; unless SEP, aliases sf and sg (dead once phase 4 ends)
     T *mu;          // R3
     T *p;           // R2
     T *gmx, *gmy, *lmu, *gfx, *gfy, *gpx, *gpy;  // R1
@@ -104,7 +106,7 @@ struct Tile {
         gg = (int *)(ga + 11 * L::NG);
         gf = gg + L::NG;
         phi = (phi_t<T> *)(sm + L::o_phi);
-        flux = (pair_t<T> *)(sm + L::o_un);
+        flux = (pair_t<T> *)(sm + L::o_flux);
         mu = (T *)(sm + L::o_mu);
         p = (T *)(sm + L::o_p);
         T *r1 = (T *)(sm + L::o_r1);
@@ -208,12 +210,10 @@ __device__ __forceinline__ void face_tail(const InstDev &I, const T (&fb)[Q], co
 
 // Flux values of the face between positions a (low side) and b = a + e_A of a
 // tile, or of the wall face of whichever of the two lies in the domain.
-template <typename T, int BX, int BY, int A, bool UNI>
-__device__ __forceinline__ void tile_face(const InstDev &I, const Tile<T, BX, BY, UNI> &S, int xa, int ya,
-                                          pair_t<T> (&F2o)[6])
+template <typename T, int A, bool UNI, typename TL>
+__device__ __forceinline__ void tile_face(const InstDev &I, const TL &S, int xa, int ya, pair_t<T> (&F2o)[6])
 {
     const ParT<T> &Pr = par<T>(I);
-    using TL = Tile<T, BX, BY, UNI>;
     constexpr int A1 = TL::L::A1;
     const int xb = xa + (A == 0 ? 1 : 0), yb = ya + (A == 1 ? 1 : 0);
     const int pa = A == 0 ? xa : ya, pb = A == 0 ? xb : yb, pt = A == 0 ? ya : xa;
@@ -301,11 +301,14 @@ __device__ __forceinline__ void tile_face(const InstDev &I, const Tile<T, BX, BY
     face_tail<T, A>(I, fb, gb, ax, true, side, area, F2o);
 }
 
-template <typename T, int BX, int BY, int MINB, bool UNI>
-__global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles,
-                                                       const AxisRecT<T> *__restrict__ geo, StepIO<T> io)
+// NT threads (a multiple of 32, at least BX * BY) share the phases of a
+// BX x BY tile; the first BX * BY of them own one cell each in the update.
+template <typename T, int BX, int BY, int NT, int MINB, bool UNI, bool SEP>
+__global__ void __launch_bounds__(NT, MINB) k_step(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles,
+                                                   const AxisRecT<T> *__restrict__ geo, StepIO<T> io)
 {
-    using TL = Tile<T, BX, BY, UNI>;
+    static_assert(NT % 32 == 0 && NT >= BX * BY, "thread count");
+    using TL = Tile<T, BX, BY, UNI, SEP>;
     using L = typename TL::L;
     extern __shared__ __align__(16) unsigned char smem[];
     TL S(smem);
@@ -314,8 +317,7 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
     const ParT<T> &Pr = par<T>(I);
     if (io.status[t.x]) return;   // masked: non-finite instance of a batch
     const int i0 = t.y, j0 = t.z;
-    const int tid = threadIdx.y * BX + threadIdx.x;
-    constexpr int NT = BX * BY;
+    const int tid = threadIdx.x;
     const long long N = io.N;
 
     // global index of every region column and row (wrapped on periodic axes,
@@ -523,16 +525,16 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
     }
     __syncthreads();
 
-    const int x = threadIdx.x, y = threadIdx.y;
+    const int x = tid % BX, y = tid / BX;
     const int gi = i0 + x, gj = j0 + y;
-    const bool own = gi < I.nx && gj < I.ny;
+    const bool own = tid < BX * BY && gi < I.nx && gj < I.ny;
     const long long c = own ? cell(gi, gj) : 0;
 
     // ---- phase 5: every face of the tile once (x faces first in the index space)
     for (int k = tid; k < L::NFT; k += NT) {
         pair_t<T> F2o[6];
-        if (k < L::NFX) tile_face<T, BX, BY, 0, UNI>(I, S, k % (BX + 1) - 1, k / (BX + 1), F2o);
-        else tile_face<T, BX, BY, 1, UNI>(I, S, (k - L::NFX) % BX, (k - L::NFX) / BX - 1, F2o);
+        if (k < L::NFX) tile_face<T, 0, UNI>(I, S, k % (BX + 1) - 1, k / (BX + 1), F2o);
+        else tile_face<T, 1, UNI>(I, S, (k - L::NFX) % BX, (k - L::NFX) / BX - 1, F2o);
 #pragma unroll
         for (int m = 0; m < 6; m++) S.flux[m * L::NFT + k] = F2o[m];
     }
@@ -558,9 +560,13 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
     const T dtv = dt / (S.c(10, 0, x) * S.c(10, 1, y));
     // tilde^{n+1} = 4/3 bar-plus - 1/3 tilde - dt/|V| J
     pair_t<T> nw[Q];
+    const int r2 = TL::i2(x, y);
 #pragma unroll
-    for (int q = 0; q < Q; q++)
-        nw[q] = pfma(pr(T(4.0 / 3.0)), S.bp[q * L::A1 + r1], pfma(pr(T(-1.0 / 3.0)), pr(io.f_in[q * N + c], io.g_in[q * N + c]), pmul(pr(-dtv), J[q])));
+    for (int q = 0; q < Q; q++) {
+        // the cell's own tilde values: still in shared memory with SEP, else an L2 hit (read in phase 1)
+        const pair_t<T> old = SEP ? pr(S.sf[q * L::A2 + r2], S.sg[q * L::A1 + r1]) : pr(io.f_in[q * N + c], io.g_in[q * N + c]);
+        nw[q] = pfma(pr(T(4.0 / 3.0)), S.bp[q * L::A1 + r1], pfma(pr(T(-1.0 / 3.0)), old, pmul(pr(-dtv), J[q])));
+    }
     bool finite = true;
     if constexpr (sizeof(T) == sizeof(double)) {
         T phi = 0;
@@ -587,7 +593,7 @@ __global__ void __launch_bounds__(BX *BY, MINB) k_step(const InstDev *__restrict
                 finite = finite && isfinite(nw[q].y);
             }
         }
-        const phi_t<T> phi = phi_add(io.phi_in[c], -(dtv * jsum));   // an L2 hit: read in phase 1
+        const phi_t<T> phi = phi_add(S.phi[TL::i4(x, y)], -(dtv * jsum));
         io.phi_out[c] = phi;
         io.g_out[c] = phi_subt(phi, gsum);
         finite = finite && isfinite(phi_val(phi));

@@ -312,7 +312,7 @@ def conservation_static(phi_ptr, dx_ptr, dy_ptr, nx, ny, params, out_ptr, stream
                                             ctypes.c_void_p(int(stream)))
 
 
-NUM_TILE_SHAPES = 3
+NUM_TILE_SHAPES = 5
 
 
 def tile_shape_name(k):
