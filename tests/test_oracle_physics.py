@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import diagnostics
 from paper_1802_02868_gb300 import inputs as I
 
 
@@ -170,6 +171,9 @@ def test_laplace_law():
         p = o.moments()["p"]
         dps[R] = p[24, 24] - p[0, 0]
         assert dps[R] * R / 1e-3 == pytest.approx(1.0, abs=0.06)
+        # the jump of the bulk means of the Laplace pressure P (oracle diagnostics)
+        d, _ = diagnostics.diagnostics(o, c.mesh, c.params)
+        assert (d["p_bulk_A"] - d["p_bulk_B"]) * R / 1e-3 == pytest.approx(1.0, abs=0.06)
     assert dps[12.0] / dps[16.0] == pytest.approx(16.0 / 12.0, rel=0.03)
 
 
