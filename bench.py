@@ -280,6 +280,27 @@ def run_reference(args, cases, desc):
     return 0
 
 
+def time_diagnostics(sim, ncells, peak_hbm, calls=5):
+    """On-device diagnostics of the final state (dugks_diagnostics: macros,
+    k_diag, per-instance finalisation, read-back), outside the timed region."""
+    from paper_1802_02868_gb300 import dugks
+    sim.set_timing(True)
+    sim.kernel_times()
+    t0 = time.perf_counter()
+    for _ in range(calls):
+        sim.diagnostics()
+    host_ms = (time.perf_counter() - t0) * 1e3 / calls
+    kt = sim.kernel_times()
+    sim.set_timing(False)
+    kms, kn = kt["k_diag"]
+    avg_s = kms / max(kn, 1) * 1e-3
+    bpc = sim.kernel_bytes_per_cell(dugks.kernel_name_index("k_diag"))
+    return {"calls": calls, "ms_per_call": host_ms,
+            "kernels_ms_per_call": {k: kt[k][0] / calls for k in ("k_mu", "k_macro", "k_diag")},
+            "k_diag_hbm": {"achieved": bpc * ncells / avg_s / 1e9, "peak": peak_hbm, "unit": "GB/s",
+                           "frac": bpc * ncells / avg_s / 1e9 / peak_hbm, "algorithmic_bytes_per_cell": bpc}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -409,6 +430,7 @@ def main():
                 ncells * 72 * (1 if prec == dugks.FP32 else 2) / 1e9) if ncells * 72 > 129e6 else
                 "inputs smaller than L2: not flushed"),
             "e2e": e2e, "gpu_launches": launches, "roofline": roof, "clocks": clk, "instances_finite": n_finite}
+    line["diagnostics"] = time_diagnostics(sim, ncells, peak_hbm)
     if rank == 0 and ws == 1 and len(cases) > 1 and prec == dugks.FP32:
         rate64, nsamp = fp64_single_instance_rate(dugks, torch, cases)
         line["speedup_vs_fp64_single_instance"] = {

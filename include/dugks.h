@@ -146,7 +146,7 @@ int dugks_launch_count(const dugks_sim *sim, long *count);
    accumulated milliseconds and launch counts per kernel with
    dugks_kernel_times (arrays of DUGKS_NUM_KERNELS entries, names by
    dugks_kernel_name).  Synchronises on read. */
-#define DUGKS_NUM_KERNELS 7
+#define DUGKS_NUM_KERNELS 8
 int dugks_set_timing(dugks_sim *sim, int enable);
 int dugks_kernel_times(dugks_sim *sim, double *ms, long *launches);
 const char *dugks_kernel_name(int k);
@@ -175,6 +175,38 @@ const char *dugks_tile_shape_name(int shape);
    step.  Setting DUGKS_GENERAL_ONLY=1 in the environment before creation sends
    every instance through the general path. */
 int dugks_uniform_instances(const dugks_sim *sim, int *n);
+
+/* Diagnostics of the current state of every instance, computed on the device
+   in FP64 (the paper's test quantities; c = (phi - phiB)/(phiA - phiB)):
+     mass        total volume of the cells with c > 1/2: the droplet mass of
+                 Sec. 3.1, Table A1 (a cell count on a unit mesh)
+     xc, yc      centroid of that region (coordinates with the low faces at
+                 0, no unwrapping across periodic boundaries), Sec. 3.3
+     ux, uy      its volume-weighted mean velocity (the rise velocity of a
+                 bubble), Sec. 3.3
+     p_bulk_A/B  volume-weighted mean of the Laplace pressure P over the cells
+                 with c > 0.9 / c < 0.1; their difference is the pressure jump
+                 of Laplace's law, Sec. 3.1
+     front_y, tip_y  highest and lowest height at which c crosses 1/2 going up
+                 a column (c < 1/2 below, >= 1/2 above, linear interpolation
+                 between the two centres; pairs across a periodic y boundary
+                 excluded): with fluid A on top, the bubble front and the spike
+                 tip of the Rayleigh-Taylor instability, Sec. 3.4
+   Undefined entries (an empty region, no crossing, a masked instance) are
+   NaN.  out holds n_instances entries (host memory).  Allocates a small
+   device buffer on the first call; synchronises. */
+typedef struct {
+    double mass, xc, yc, ux, uy, p_bulk_A, p_bulk_B, front_y, tip_y;
+} dugks_diag;
+int dugks_diagnostics(dugks_sim *sim, dugks_diag *out);
+
+/* The Laplace pressure field of Sec. 3.1, P = p0 - kappa phi lap(phi)
+   + kappa |grad phi|^2 / 2 + p with p0 = phi psi' - psi and
+   psi = beta (phi - phiA)^2 (phi - phiB)^2, in FP64 on the device; the
+   gradients use the stencils of Eqs. (nonphi), (nonphi2) with mirror ghosts
+   at walls.  P (host) holds all instances' cells, row-major, in instance
+   order.  Synchronises. */
+int dugks_laplace_pressure(dugks_sim *sim, double *P);
 
 const char *dugks_status_str(int status);
 

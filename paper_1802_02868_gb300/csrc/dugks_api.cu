@@ -17,6 +17,7 @@
 #include "dugks_kernels.cuh"
 #include "dugks_fused.cuh"
 #include "dugks_adjoint.cuh"
+#include "dugks_diag.cuh"
 
 using namespace dugks;
 
@@ -67,6 +68,8 @@ struct dugks_sim {
     double2 *d_sums = nullptr;
     double *d_stage = nullptr;    // dense FP64 staging [5][n_dense]
     double *d_init_in = nullptr;  // the last init inputs phi, ux, uy, p [4][n_dense] (for the adjoint)
+    DiagPart *d_diag_parts = nullptr;   // per tile (allocated by the first diagnostics call)
+    DiagOut *d_diag_out = nullptr;      // per instance
     bool has_init = false;
     Planes<double> P64{};
     Planes<float> P32{};
@@ -93,7 +96,7 @@ const ShapeDesc kShapes[DUGKS_NUM_TILE_SHAPES] = {{32, 8, 256, 0, "32x8"},
                                                   {32, 8, 352, 1, "32x8/352 sep"},
                                                   {32, 8, 384, 1, "32x8/384 sep"}};
 
-const char *kNames[K_COUNT] = {"k_mu", "k_macro", "k_cell", "k_face", "k_init", "k_reduce", "k_step"};
+const char *kNames[K_COUNT] = {"k_mu", "k_macro", "k_cell", "k_face", "k_init", "k_reduce", "k_step", "k_diag"};
 
 int cuda_status(cudaError_t e)
 {
@@ -131,10 +134,13 @@ int validate(const dugks_mesh &m, const dugks_params &p)
 void axis_records(int n, const double *d, int bc, std::vector<AxisRec> &out)
 {
     const bool wall = bc == DUGKS_BC_WALL;
+    double edge = 0.0;   // high face of the previous cell
     for (int k = 0; k < n; k++) {
         AxisRec r;
         std::memset(&r, 0, sizeof(r));
         r.d = d[k];
+        edge += d[k];
+        r.xc = edge - 0.5 * d[k];
         bool has_m = true, has_p = true;
         int km, kp;
         double dl, dr;
@@ -502,6 +508,30 @@ int do_reduce(dugks_sim *s)
     return cuda_status(cudaGetLastError());
 }
 
+// Diagnostics: macros (k_mu, k_macro), then k_diag per tile (optionally the
+// dense P field into p_dense) and k_diag_inst per instance.
+template <typename T>
+int do_diag(dugks_sim *s, double *p_dense)
+{
+    if (!s->d_diag_parts) {
+        cudaError_t e = cudaMalloc(&s->d_diag_parts, sizeof(DiagPart) * s->n_tiles);
+        if (e == cudaSuccess) e = cudaMalloc(&s->d_diag_out, sizeof(DiagOut) * s->n_inst);
+        if (e != cudaSuccess) {
+            cudaFree(s->d_diag_parts);
+            s->d_diag_parts = nullptr;
+            return cuda_status(e);
+        }
+    }
+    Planes<T> &P = planes<T>(s);
+    const dim3 blk(TX, TY);
+    const unsigned g = (unsigned)s->n_tiles;
+    { Timed t(s, K_MU); k_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P); }
+    { Timed t(s, K_MACRO); k_macro<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, 0); }
+    { Timed t(s, K_DIAG); k_diag<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, s->d_diag_parts, p_dense, s->d_dense0); }
+    { Timed t(s, -1); k_diag_inst<<<(unsigned)s->n_inst, DIAG_INST_THREADS, 0, s->stream>>>(s->d_inst, s->d_status, s->d_diag_parts, s->d_diag_out); }
+    return cuda_status(cudaGetLastError());
+}
+
 template <typename T>
 void assign_planes(dugks_sim *s, Planes<T> &P, T *base)
 {
@@ -542,6 +572,8 @@ void free_sim(dugks_sim *s)
     cudaFree(s->d_sums);
     cudaFree(s->d_stage);
     cudaFree(s->d_init_in);
+    cudaFree(s->d_diag_parts);
+    cudaFree(s->d_diag_out);
     if (s->graph2) cudaGraphExecDestroy(s->graph2);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     for (auto &e : s->ev_used) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
@@ -939,6 +971,40 @@ int dugks_moments(dugks_sim *s, double *phi, double *rho, double *ux, double *uy
     return sync_status(s);
 }
 
+int dugks_diagnostics(dugks_sim *s, dugks_diag *out)
+{
+    if (!s || !out) return DUGKS_ERR_ARG;
+    int rc = s->prec == DUGKS_FP64 ? do_diag<double>(s, nullptr) : do_diag<float>(s, nullptr);
+    if (rc) return rc;
+    std::vector<DiagOut> h(s->n_inst);
+    cudaError_t e = cudaMemcpyAsync(h.data(), s->d_diag_out, sizeof(DiagOut) * s->n_inst, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int k = 0; k < s->n_inst; k++) {
+        const DiagOut &d = h[k];
+        out[k].mass = d.mass;
+        out[k].xc = d.xc;
+        out[k].yc = d.yc;
+        out[k].ux = d.ux;
+        out[k].uy = d.uy;
+        out[k].p_bulk_A = d.p_bulk_A;
+        out[k].p_bulk_B = d.p_bulk_B;
+        out[k].front_y = d.front_y;
+        out[k].tip_y = d.tip_y;
+    }
+    return sync_status(s);
+}
+
+int dugks_laplace_pressure(dugks_sim *s, double *P)
+{
+    if (!s || !P) return DUGKS_ERR_ARG;
+    int rc = s->prec == DUGKS_FP64 ? do_diag<double>(s, s->d_stage) : do_diag<float>(s, s->d_stage);
+    if (rc) return rc;
+    cudaError_t e = cudaMemcpyAsync(P, s->d_stage, sizeof(double) * s->n_dense, cudaMemcpyDeviceToHost, s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    return sync_status(s);
+}
+
 int dugks_conservation(dugks_sim *s, double *sum_phi, double *sum_rho)
 {
     if (!s) return DUGKS_ERR_ARG;
@@ -1065,6 +1131,7 @@ int dugks_kernel_bytes_per_cell(const dugks_sim *s, int k, double *bytes)
     case K_INIT: b = 8 + 4 * w + 18 * w; break;
     case K_REDUCE: b = 8; break;
     case K_STEP: b = 2 * (2 * Q) * w + 16; break;                   // tilde f, g and phi, read once and written once
+    case K_DIAG: b = 8 + 3 * w; break;                               // phi, p, ux, uy (the P field adds 8 written)
     }
     *bytes = b;
     return DUGKS_OK;

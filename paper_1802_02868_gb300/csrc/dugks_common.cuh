@@ -35,7 +35,7 @@ struct AxisRec {
     double wL, wR, invd;
     int km, kp;       // neighbour indices (periodic wrap; self for a wall ghost)
     int lo_wall, hi_wall;
-    double pad_;
+    double xc;        // cell-centre coordinate (the low face of the axis at 0)
 };
 static_assert(sizeof(AxisRec) == 128, "AxisRec layout");
 
@@ -179,6 +179,6 @@ struct Planes {
 constexpr int TX = 32;
 constexpr int TY = 8;
 
-enum KernelId { K_MU = 0, K_MACRO = 1, K_CELL = 2, K_FACE = 3, K_INIT = 4, K_REDUCE = 5, K_STEP = 6, K_COUNT = 7 };
+enum KernelId { K_MU = 0, K_MACRO = 1, K_CELL = 2, K_FACE = 3, K_INIT = 4, K_REDUCE = 5, K_STEP = 6, K_DIAG = 7, K_COUNT = 8 };
 
 }  // namespace dugks

@@ -41,10 +41,17 @@ class Mesh_t(ctypes.Structure):
                 ("dy", ctypes.POINTER(ctypes.c_double)), ("bc_x", ctypes.c_int), ("bc_y", ctypes.c_int)]
 
 
+DIAG_FIELDS = ("mass", "xc", "yc", "ux", "uy", "p_bulk_A", "p_bulk_B", "front_y", "tip_y")
+
+
 class Params_t(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in ("phiA", "phiB", "rhoA", "rhoB", "nuA", "nuB", "mobility", "tau_g",
                                                "beta", "kappa", "gx", "gy", "rho_ref", "cfl")] + \
                [("precision", ctypes.c_int)]
+
+
+class Diag_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in DIAG_FIELDS]
 
 
 _lib = None
@@ -53,7 +60,7 @@ EXPORTS = ("dugks_create", "dugks_batch_create", "dugks_destroy", "dugks_init", 
            "dugks_launch_count", "dugks_set_timing", "dugks_kernel_times", "dugks_kernel_name",
            "dugks_kernel_bytes_per_cell", "dugks_status_str", "dugks_conservation_static",
            "dugks_autotune", "dugks_set_tile_shape", "dugks_tile_shape", "dugks_tile_shape_name",
-           "dugks_adjoint", "dugks_uniform_instances")
+           "dugks_adjoint", "dugks_uniform_instances", "dugks_diagnostics", "dugks_laplace_pressure")
 STATIC_MAX_CELLS = 16777216
 
 
@@ -98,6 +105,8 @@ def load(build_if_missing: bool = True):
     L.dugks_set_tile_shape.argtypes = [vp, ip]
     L.dugks_tile_shape.argtypes = [vp] + [ctypes.POINTER(ctypes.c_int)] * 3
     L.dugks_uniform_instances.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.dugks_diagnostics.argtypes = [vp, ctypes.POINTER(Diag_t)]
+    L.dugks_laplace_pressure.argtypes = [vp, dp]
     L.dugks_tile_shape_name.argtypes = [ip]
     L.dugks_tile_shape_name.restype = ctypes.c_char_p
     L.dugks_status_str.argtypes = [ip]
@@ -109,7 +118,7 @@ def load(build_if_missing: bool = True):
     return L
 
 
-NUM_KERNELS = 7
+NUM_KERNELS = 8
 
 
 def _check(fn, rc):
@@ -244,6 +253,21 @@ class Sim:
             raise ValueError("state has %d cells, expected %d" % (buf.shape[2], self.ncells))
         _check("dugks_load", load().dugks_load(self.h, buf.ctypes.data_as(ctypes.c_void_p), buf.nbytes))
 
+    def diagnostics(self):
+        """Per-instance diagnostics (dugks_diagnostics) as dicts; one dict for a
+        single instance."""
+        n = len(self.meshes)
+        out = (Diag_t * n)()
+        _check("dugks_diagnostics", load().dugks_diagnostics(self.h, out))
+        ds = [{k: getattr(d, k) for k in DIAG_FIELDS} for d in out]
+        return ds[0] if self.single else ds
+
+    def laplace_pressure(self):
+        """The Laplace pressure field P of every instance (dugks_laplace_pressure)."""
+        out = np.zeros(self.ncells)
+        _check("dugks_laplace_pressure", load().dugks_laplace_pressure(self.h, _dp(out)))
+        return self._split(out)
+
     def uniform_instances(self):
         """Instances on the fused step's uniform periodic path."""
         v = ctypes.c_int()
@@ -321,6 +345,13 @@ def tile_shape_name(k):
 
 def kernel_name(k):
     return load().dugks_kernel_name(int(k)).decode()
+
+
+def kernel_name_index(name):
+    for k in range(NUM_KERNELS):
+        if kernel_name(k) == name:
+            return k
+    raise KeyError(name)
 
 
 def status_str(rc):
