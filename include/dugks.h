@@ -110,6 +110,22 @@ int dugks_conservation(dugks_sim *sim, double *sum_phi, double *sum_rho);
    last init; array of n_instances ints.  Synchronises. */
 int dugks_batch_status(dugks_sim *sim, int *per_instance_status);
 
+/* Hold instances of a batch still: paused[k] != 0 pauses instance k,
+   0 resumes it (host array of n_instances ints).  A paused instance keeps its
+   state through dugks_step while the others advance; dugks_moments,
+   dugks_conservation and the diagnostics still report it.  dugks_init resumes
+   every instance; dugks_adjoint refuses a batch with a paused instance
+   (DUGKS_ERR_ARG).  Synchronises. */
+int dugks_batch_set_paused(dugks_sim *sim, const int *paused);
+
+/* Advance instance k by nsteps[k] >= 0 steps (host array of n_instances
+   longs): the batch steps max(nsteps) times, each instance pausing once its
+   count is reached, so that instances with different time steps (a CFL
+   sweep) can be brought to the same time.  Instances paused before the call
+   stay paused and keep their pause afterwards.  Synchronises between the
+   segments of equal counts. */
+int dugks_batch_step_each(dugks_sim *sim, const long *nsteps);
+
 /* Time step dt of instance k (Eq. cfl). */
 int dugks_dt(const dugks_sim *sim, int instance, double *dt);
 

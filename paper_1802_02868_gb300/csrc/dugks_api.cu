@@ -425,8 +425,8 @@ int launch_step(dugks_sim *s)
     Planes<T> &P = planes<T>(s);
     const dim3 blk(TX, TY);
     const unsigned g = (unsigned)s->n_tiles;
-    { Timed t(s, K_MU); k_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P); }
-    { Timed t(s, K_MACRO); k_macro<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, 0); }
+    { Timed t(s, K_MU); k_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, (const AxisRecT<T> *)s->d_geoT, P); }
+    { Timed t(s, K_MACRO); k_macro<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, (const AxisRecT<T> *)s->d_geoT, P, 0); }
     { Timed t(s, K_CELL); k_cell<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P); }
     { Timed t(s, K_FACE); k_face<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P); }
     return cuda_status(cudaGetLastError());
@@ -443,7 +443,7 @@ int do_init(dugks_sim *s)
     { Timed t(s, -1); k_unpack<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_stage + 1 * D, P.ux, s->d_dense0); }
     { Timed t(s, -1); k_unpack<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_stage + 2 * D, P.uy, s->d_dense0); }
     { Timed t(s, -1); k_unpack<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_stage + 3 * D, P.p, s->d_dense0); }
-    { Timed t(s, K_MU); k_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P); }
+    { Timed t(s, K_MU); k_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, (const AxisRecT<T> *)s->d_geoT, P); }
     { Timed t(s, K_INIT); k_init<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P); }
     // FP64: phi = sum g of the new state, as the next step recomputes it; FP32:
     // the given phi stays the authoritative FP64 order parameter
@@ -458,8 +458,8 @@ int do_moments(dugks_sim *s)
     const dim3 blk(TX, TY);
     const unsigned g = (unsigned)s->n_tiles;
     const long long D = s->n_dense;
-    { Timed t(s, K_MU); k_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P); }
-    { Timed t(s, K_MACRO); k_macro<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, 1); }
+    { Timed t(s, K_MU); k_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, (const AxisRecT<T> *)s->d_geoT, P); }
+    { Timed t(s, K_MACRO); k_macro<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, (const AxisRecT<T> *)s->d_geoT, P, 1); }
     { Timed t(s, -1); k_pack_phi<phi_t<T>><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, P.phi, s->d_stage, s->d_dense0); }
     T *src[4] = {P.rho, P.ux, P.uy, P.p};
     for (int k = 0; k < 4; k++) {
@@ -525,9 +525,10 @@ int do_diag(dugks_sim *s, double *p_dense)
     Planes<T> &P = planes<T>(s);
     const dim3 blk(TX, TY);
     const unsigned g = (unsigned)s->n_tiles;
-    { Timed t(s, K_MU); k_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P); }
-    { Timed t(s, K_MACRO); k_macro<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, 0); }
-    { Timed t(s, K_DIAG); k_diag<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, s->d_diag_parts, p_dense, s->d_dense0); }
+    { Timed t(s, K_MU); k_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, (const AxisRecT<T> *)s->d_geoT, P); }
+    { Timed t(s, K_MACRO); k_macro<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, (const AxisRecT<T> *)s->d_geoT, P, 0); }
+    { Timed t(s, K_DIAG); k_diag<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, (const AxisRecT<T> *)s->d_geoT, s->d_geo, P,
+                                                                s->d_diag_parts, p_dense, s->d_dense0); }
     { Timed t(s, -1); k_diag_inst<<<(unsigned)s->n_inst, DIAG_INST_THREADS, 0, s->stream>>>(s->d_inst, s->d_status, s->d_diag_parts, s->d_diag_out); }
     return cuda_status(cudaGetLastError());
 }
@@ -592,7 +593,7 @@ int sync_status(dugks_sim *s)
     std::vector<int> st(s->n_inst);
     e = cudaMemcpy(st.data(), s->d_status, sizeof(int) * s->n_inst, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_status(e);
-    for (int v : st) if (v) return DUGKS_ERR_NONFINITE;
+    for (int v : st) if (v & ST_NONFINITE) return DUGKS_ERR_NONFINITE;
     return DUGKS_OK;
 }
 
@@ -693,8 +694,8 @@ int adjoint_impl(dugks_sim *s, long nsteps, int K, const double *target_h, doubl
         }
         for (long k = len - 1; k >= 0 && !rc; k--) {
             copy_state<T>(s, P.f, P.phi, sg_fg(k), sg_phi(k), w.fg_bytes, w.phi_bytes);
-            k_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P);
-            k_macro<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, 0);
+            k_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, (const AxisRecT<T> *)s->d_geoT, P);
+            k_macro<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, (const AxisRecT<T> *)s->d_geoT, P, 0);
             k_cell<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P);
             cudaMemsetAsync(w.bp, 0, sizeof(T) * 2 * Q * (size_t)N, s->stream);
             cudaMemsetAsync(w.scal, 0, sizeof(T) * scal_planes * (size_t)N, s->stream);
@@ -718,7 +719,7 @@ int adjoint_impl(dugks_sim *s, long nsteps, int K, const double *target_h, doubl
         k_unpack<T><<<g, b2, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_init_in + D, P.ux, s->d_dense0);
         k_unpack<T><<<g, b2, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_init_in + 2 * D, P.uy, s->d_dense0);
         k_unpack<T><<<g, b2, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_init_in + 3 * D, P.p, s->d_dense0);
-        k_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P);
+        k_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, (const AxisRecT<T> *)s->d_geoT, P);
         cudaMemsetAsync(w.scal, 0, sizeof(T) * scal_planes * (size_t)N, s->stream);
         A.xf = xb; A.xg = xb + (size_t)Q * N;
         ka_init<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, A);
@@ -763,6 +764,14 @@ int dugks_adjoint(dugks_sim *s, long nsteps, int ckpt_every, const double *phi_t
 {
     if (!s || !phi_target || nsteps < 1 || ckpt_every < 1) return DUGKS_ERR_ARG;
     if (!s->has_init) return DUGKS_ERR_ARG;
+    {   // the reverse sweep has no notion of a paused instance
+        std::vector<int> st(s->n_inst);
+        cudaError_t e = cudaStreamSynchronize(s->stream);
+        if (e == cudaSuccess) e = cudaMemcpy(st.data(), s->d_status, sizeof(int) * s->n_inst, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_status(e);
+        for (int v : st)
+            if (v & ST_PAUSED) return DUGKS_ERR_ARG;
+    }
     const int K = (int)std::min<long>(ckpt_every, nsteps);
     return s->prec == DUGKS_FP64 ? adjoint_impl<double>(s, nsteps, K, phi_target, loss, dL_dphi0, dL_dkappa, dL_dlambda)
                                  : adjoint_impl<float>(s, nsteps, K, phi_target, loss, dL_dphi0, dL_dkappa, dL_dlambda);
@@ -865,10 +874,10 @@ int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *para
     std::vector<AxisRecT<float>> g32;
     for (const AxisRec &r : geo) {
         AxisRecT<double> a{r.d, r.c1m, r.c10, r.c1p, r.c2m, r.c20, r.c2p, r.e1m, r.e10, r.e1p, r.wL, r.wR, r.invd,
-                           r.km, r.kp, r.lo_wall, r.hi_wall};
+                           r.km, r.kp, r.lo_wall, r.hi_wall, r.xc};
         AxisRecT<float> b{(float)r.d, (float)r.c1m, (float)r.c10, (float)r.c1p, (float)r.c2m, (float)r.c20,
                           (float)r.c2p, (float)r.e1m, (float)r.e10, (float)r.e1p, (float)r.wL, (float)r.wR,
-                          (float)r.invd, r.km, r.kp, r.lo_wall, r.hi_wall};
+                          (float)r.invd, r.km, r.kp, r.lo_wall, r.hi_wall, (float)r.xc};
         g64.push_back(a);
         g32.push_back(b);
     }
@@ -1029,8 +1038,67 @@ int dugks_batch_status(dugks_sim *s, int *per_instance_status)
     std::vector<int> st(s->n_inst);
     e = cudaMemcpy(st.data(), s->d_status, sizeof(int) * s->n_inst, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_status(e);
-    for (int k = 0; k < s->n_inst; k++) per_instance_status[k] = st[k] ? DUGKS_ERR_NONFINITE : DUGKS_OK;
+    for (int k = 0; k < s->n_inst; k++) per_instance_status[k] = (st[k] & ST_NONFINITE) ? DUGKS_ERR_NONFINITE : DUGKS_OK;
     return DUGKS_OK;
+}
+
+namespace {
+// read, change and write back the paused bit of every instance (synchronises)
+int rewrite_paused(dugks_sim *s, const std::vector<char> &paused)
+{
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    std::vector<int> st(s->n_inst);
+    if (e == cudaSuccess) e = cudaMemcpy(st.data(), s->d_status, sizeof(int) * s->n_inst, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (int k = 0; k < s->n_inst; k++) st[k] = (st[k] & ~ST_PAUSED) | (paused[k] ? ST_PAUSED : 0);
+    e = cudaMemcpy(s->d_status, st.data(), sizeof(int) * s->n_inst, cudaMemcpyHostToDevice);
+    return cuda_status(e);
+}
+
+int read_paused(dugks_sim *s, std::vector<char> &paused)
+{
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    std::vector<int> st(s->n_inst);
+    if (e == cudaSuccess) e = cudaMemcpy(st.data(), s->d_status, sizeof(int) * s->n_inst, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    paused.resize(s->n_inst);
+    for (int k = 0; k < s->n_inst; k++) paused[k] = (st[k] & ST_PAUSED) ? 1 : 0;
+    return DUGKS_OK;
+}
+}  // namespace
+
+int dugks_batch_set_paused(dugks_sim *s, const int *paused)
+{
+    if (!s || !paused) return DUGKS_ERR_ARG;
+    std::vector<char> p(s->n_inst);
+    for (int k = 0; k < s->n_inst; k++) p[k] = paused[k] ? 1 : 0;
+    return rewrite_paused(s, p);
+}
+
+int dugks_batch_step_each(dugks_sim *s, const long *nsteps)
+{
+    if (!s || !nsteps) return DUGKS_ERR_ARG;
+    for (int k = 0; k < s->n_inst; k++)
+        if (nsteps[k] < 0) return DUGKS_ERR_ARG;
+    std::vector<char> orig;
+    int rc = read_paused(s, orig);
+    if (rc) return rc;
+    std::vector<long> targets(nsteps, nsteps + s->n_inst);
+    std::sort(targets.begin(), targets.end());
+    targets.erase(std::unique(targets.begin(), targets.end()), targets.end());
+    long done = 0;
+    std::vector<char> p(s->n_inst);
+    for (long T : targets) {
+        if (T <= done) continue;
+        // an instance whose count is reached holds still for the rest
+        for (int k = 0; k < s->n_inst; k++) p[k] = orig[k] || nsteps[k] <= done;
+        rc = rewrite_paused(s, p);
+        if (rc == DUGKS_OK) rc = dugks_step(s, T - done);
+        if (rc) break;
+        done = T;
+    }
+    const int rc2 = rewrite_paused(s, orig);
+    return rc ? rc : rc2;
 }
 
 int dugks_dt(const dugks_sim *s, int instance, double *dt)

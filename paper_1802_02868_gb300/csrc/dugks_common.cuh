@@ -104,6 +104,7 @@ template <typename T>
 struct AxisRecT {
     T d, c1m, c10, c1p, c2m, c20, c2p, e1m, e10, e1p, wL, wR, invd;
     int km, kp, lo_wall, hi_wall;
+    T xc;
 };
 
 // A pair (f, g) of values of the two distribution kinds.  In FP32 the pair
@@ -178,6 +179,12 @@ struct Planes {
 
 constexpr int TX = 32;
 constexpr int TY = 8;
+
+// Per-instance status bits: set by the kernels when a non-finite value
+// appears (the instance is masked from then on), and by the host to hold an
+// instance still while the rest of a batch steps.
+constexpr int ST_NONFINITE = 1;
+constexpr int ST_PAUSED = 2;
 
 enum KernelId { K_MU = 0, K_MACRO = 1, K_CELL = 2, K_FACE = 3, K_INIT = 4, K_REDUCE = 5, K_STEP = 6, K_DIAG = 7, K_COUNT = 8 };
 

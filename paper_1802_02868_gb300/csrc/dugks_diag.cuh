@@ -33,81 +33,90 @@ struct DiagOut {
 
 __device__ __forceinline__ double diag_nan() { return __longlong_as_double(0x7ff8000000000000LL); }
 
+// Arithmetic in the sim's precision T: FP32 sims sum each warp in FP32 (the
+// FP64 pipe of GB300 runs at 1/64 of the FP32 rate) and add the warps in FP64;
+// the crossing heights are placed and compared in FP64.
 template <typename T>
 __global__ void __launch_bounds__(TX *TY) k_diag(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles,
-                                                 const AxisRec *__restrict__ geo, Planes<T> P, DiagPart *parts,
-                                                 double *p_dense, const long long *__restrict__ dense0)
+                                                 const AxisRecT<T> *__restrict__ geoT, const AxisRec *__restrict__ geo,
+                                                 Planes<T> P, DiagPart *parts, double *p_dense,
+                                                 const long long *__restrict__ dense0)
 {
-    __shared__ double red[TX * TY / 32][DIAG_SUMS + 2];
+    __shared__ double red[TX * TY / 32][DIAG_SUMS];
+    __shared__ unsigned long long s_front, s_tip;   // bit patterns of positive doubles order as integers
+    __shared__ int s_ncross;
     const int4 t = tiles[blockIdx.x];
     const InstDev &I = insts[t.x];
+    const ParT<T> &Pr = par<T>(I);
     const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
-    double v[DIAG_SUMS];
+    const int tid = threadIdx.y * TX + threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        s_front = 0ull;
+        s_tip = 0x7ff0000000000000ull;   // +inf
+        s_ncross = 0;
+    }
+    __syncthreads();
+    T v[DIAG_SUMS];
 #pragma unroll
-    for (int k = 0; k < DIAG_SUMS; k++) v[k] = 0.0;
-    double front = -INFINITY, tip = INFINITY;
-    if (!P.status[t.x] && i < I.nx && j < I.ny) {
-        const AxisRec &ax = geo[I.gx_off + i];
-        const AxisRec &ay = geo[I.gy_off + j];
+    for (int k = 0; k < DIAG_SUMS; k++) v[k] = T(0);
+    if (!(P.status[t.x] & ST_NONFINITE) && i < I.nx && j < I.ny) {
+        const AxisRecT<T> &ax = geoT[I.gx_off + i];
+        const AxisRecT<T> &ay = geoT[I.gy_off + j];
         const long long c = cell_of(I, i, j);
-        const double f0 = phi_to_double(P.phi[c]);
-        const double fxm = phi_to_double(P.phi[cell_of(I, ax.km, j)]) - f0;
-        const double fxp = phi_to_double(P.phi[cell_of(I, ax.kp, j)]) - f0;
-        const double fym = phi_to_double(P.phi[cell_of(I, i, ay.km)]) - f0;
-        const double fyp = phi_to_double(P.phi[cell_of(I, i, ay.kp)]) - f0;
-        const double gx = ax.c1m * fxm + ax.c1p * fxp;
-        const double gy = ay.c1m * fym + ay.c1p * fyp;
-        const double lap = (ax.c2m * fxm + ax.c2p * fxp) + (ay.c2m * fym + ay.c2p * fyp);
-        const double a = f0 - I.phiA, b = f0 - I.phiB;
-        const double psi = I.beta * a * a * b * b;
-        const double dpsi = 2.0 * I.beta * a * b * (a + b);
-        const double Pv = (f0 * dpsi - psi) - I.kappa * f0 * lap + 0.5 * I.kappa * (gx * gx + gy * gy) + (double)P.p[c];
-        if (p_dense) p_dense[dense0[t.x] + (long long)j * I.nx + i] = Pv;
-        const double vol = ax.d * ay.d;
-        const double cn = (f0 - I.phiB) / (I.phiA - I.phiB);
-        if (cn > 0.5) {
+        const phi_t<T> p0 = P.phi[c];
+        const T fxm = phi_sub(P.phi[cell_of(I, ax.km, j)], p0), fxp = phi_sub(P.phi[cell_of(I, ax.kp, j)], p0);
+        const T fym = phi_sub(P.phi[cell_of(I, i, ay.km)], p0), fyp = phi_sub(P.phi[cell_of(I, i, ay.kp)], p0);
+        const T gx = ax.c1m * fxm + ax.c1p * fxp;
+        const T gy = ay.c1m * fym + ay.c1p * fyp;
+        const T lap = (ax.c2m * fxm + ax.c2p * fxp) + (ay.c2m * fym + ay.c2p * fyp);
+        const T f0 = T(phi_val(p0));
+        const T a = f0 - Pr.phiA, b = f0 - Pr.phiB;
+        const T psi = Pr.beta * a * a * b * b;
+        const T dpsi = T(2) * Pr.beta * a * b * (a + b);
+        const T Pv = (f0 * dpsi - psi) - Pr.kappa * f0 * lap + T(0.5) * Pr.kappa * (gx * gx + gy * gy) + P.p[c];
+        if (p_dense) p_dense[dense0[t.x] + (long long)j * I.nx + i] = (double)Pv;
+        const T vol = ax.d * ay.d;
+        const T inv = T(1) / (Pr.phiA - Pr.phiB);
+        const T cn = b * inv;
+        if (cn > T(0.5)) {
             v[0] = vol;
             v[1] = vol * ax.xc;
             v[2] = vol * ay.xc;
-            v[3] = vol * (double)P.ux[c];
-            v[4] = vol * (double)P.uy[c];
+            v[3] = vol * P.ux[c];
+            v[4] = vol * P.uy[c];
         }
-        if (cn > 0.9) { v[5] = vol * Pv; v[6] = vol; }
-        if (cn < 0.1) { v[7] = vol * Pv; v[8] = vol; }
-        if (j + 1 < I.ny && cn < 0.5) {
-            const double c1 = (phi_to_double(P.phi[cell_of(I, i, j + 1)]) - I.phiB) / (I.phiA - I.phiB);
-            if (c1 >= 0.5) {
-                const double y1 = geo[I.gy_off + j + 1].xc;
-                front = tip = ay.xc + (0.5 - cn) / (c1 - cn) * (y1 - ay.xc);
+        if (cn > T(0.9)) { v[5] = vol * Pv; v[6] = vol; }
+        if (cn < T(0.1)) { v[7] = vol * Pv; v[8] = vol; }
+        if (j + 1 < I.ny && cn < T(0.5)) {
+            const T c1 = (T(phi_val(P.phi[cell_of(I, i, j + 1)])) - Pr.phiB) * inv;
+            if (c1 >= T(0.5)) {
+                const double y0 = geo[I.gy_off + j].xc, y1 = geo[I.gy_off + j + 1].xc;
+                const double y = y0 + (double)((T(0.5) - cn) / (c1 - cn)) * (y1 - y0);
+                const unsigned long long bits = (unsigned long long)__double_as_longlong(y);
+                atomicMax(&s_front, bits);
+                atomicMin(&s_tip, bits);
+                atomicAdd(&s_ncross, 1);
             }
         }
     }
-    // fixed-order reduction: warp shuffles, then the warps in order
+    // fixed-order reduction: warp shuffles in T, then the warps in order in FP64
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
         for (int k = 0; k < DIAG_SUMS; k++) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-        front = fmax(front, __shfl_down_sync(0xffffffffu, front, o));
-        tip = fmin(tip, __shfl_down_sync(0xffffffffu, tip, o));
     }
-    const int tid = threadIdx.y * TX + threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (lane == 0) {
 #pragma unroll
-        for (int k = 0; k < DIAG_SUMS; k++) red[warp][k] = v[k];
-        red[warp][DIAG_SUMS] = front;
-        red[warp][DIAG_SUMS + 1] = tip;
+        for (int k = 0; k < DIAG_SUMS; k++) red[warp][k] = (double)v[k];
     }
     __syncthreads();
     if (tid == 0) {
         DiagPart out;
         for (int k = 0; k < DIAG_SUMS; k++) out.s[k] = red[0][k];
-        out.front = red[0][DIAG_SUMS];
-        out.tip = red[0][DIAG_SUMS + 1];
-        for (int w = 1; w < TX * TY / 32; w++) {
+        for (int w = 1; w < TX * TY / 32; w++)
             for (int k = 0; k < DIAG_SUMS; k++) out.s[k] += red[w][k];
-            out.front = fmax(out.front, red[w][DIAG_SUMS]);
-            out.tip = fmin(out.tip, red[w][DIAG_SUMS + 1]);
-        }
+        out.front = s_ncross ? __longlong_as_double((long long)s_front) : -INFINITY;
+        out.tip = s_ncross ? __longlong_as_double((long long)s_tip) : INFINITY;
         parts[blockIdx.x] = out;
     }
 }
@@ -140,7 +149,7 @@ __global__ void __launch_bounds__(DIAG_INST_THREADS) k_diag_inst(const InstDev *
     }
     const double nan = diag_nan();
     DiagOut o;
-    if (status[blockIdx.x]) {
+    if (status[blockIdx.x] & ST_NONFINITE) {
         o.mass = o.xc = o.yc = o.ux = o.uy = o.p_bulk_A = o.p_bulk_B = o.front_y = o.tip_y = nan;
     } else {
         const double m = a.s[0];

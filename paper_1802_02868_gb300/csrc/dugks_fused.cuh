@@ -315,9 +315,25 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const InstDev *__restrict__ i
     const int4 t = tiles[blockIdx.x];
     const InstDev &I = insts[t.x];
     const ParT<T> &Pr = par<T>(I);
-    if (io.status[t.x]) return;   // masked: non-finite instance of a batch
     const int i0 = t.y, j0 = t.z;
     const int tid = threadIdx.x;
+    {
+        const int st = io.status[t.x];
+        if (st & ST_NONFINITE) return;   // masked: non-finite instance of a batch
+        if (st & ST_PAUSED) {            // paused: the state passes to the other buffer unchanged
+            const int x = tid % BX, y = tid / BX;
+            if (tid < BX * BY && i0 + x < I.nx && j0 + y < I.ny) {
+                const long long c = I.cell0 + (long long)(j0 + y) * I.nxp + (i0 + x);
+#pragma unroll
+                for (int q = 0; q < Q; q++) {
+                    io.f_out[q * io.N + c] = io.f_in[q * io.N + c];
+                    io.g_out[q * io.N + c] = io.g_in[q * io.N + c];
+                }
+                io.phi_out[c] = io.phi_in[c];
+            }
+            return;
+        }
+    }
     const long long N = io.N;
 
     // global index of every region column and row (wrapped on periodic axes,

@@ -120,16 +120,16 @@ __device__ __forceinline__ void eq_src(const InstDev &I, const Pt<T> &s, int q, 
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(TX *TY) k_mu(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles,
-                                               const AxisRec *__restrict__ geo, Planes<T> P)
+                                               const AxisRecT<T> *__restrict__ geo, Planes<T> P)
 {
     const int4 t = tiles[blockIdx.x];
     const InstDev &I = insts[t.x];
     const ParT<T> &Pr = par<T>(I);
-    if (P.status[t.x]) return;   // masked: non-finite instance of a batch
+    if (P.status[t.x] & ST_NONFINITE) return;   // masked: non-finite instance of a batch (a paused one still gets its macros)
     const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
     if (i >= I.nx || j >= I.ny) return;
-    const AxisRec &ax = geo[I.gx_off + i];
-    const AxisRec &ay = geo[I.gy_off + j];
+    const auto &ax = geo[I.gx_off + i];
+    const auto &ay = geo[I.gy_off + j];
     const long long c = cell_of(I, i, j);
     // Differences of the stored phi are formed first, so that the Laplacian
     // keeps the precision of the stored phi in FP32 mode (the stencil weights
@@ -143,18 +143,18 @@ __global__ void __launch_bounds__(TX *TY) k_mu(const InstDev *__restrict__ insts
 }
 
 // first derivatives of a cell field along x and y (mirror ghosts)
-template <typename T>
-__device__ __forceinline__ void grad_field(const InstDev &I, const T *__restrict__ F, const AxisRec &ax,
-                                           const AxisRec &ay, int i, int j, T f0, T &gx, T &gy)
+template <typename T, typename R>
+__device__ __forceinline__ void grad_field(const InstDev &I, const T *__restrict__ F, const R &ax,
+                                           const R &ay, int i, int j, T f0, T &gx, T &gy)
 {
     gx = T(ax.c1m) * F[cell_of(I, ax.km, j)] + T(ax.c10) * f0 + T(ax.c1p) * F[cell_of(I, ax.kp, j)];
     gy = T(ay.c1m) * F[cell_of(I, i, ay.km)] + T(ay.c10) * f0 + T(ay.c1p) * F[cell_of(I, i, ay.kp)];
 }
 
 // first derivatives of the stored order parameter, difference form (weights sum to zero)
-template <typename T>
-__device__ __forceinline__ void grad_phi(const InstDev &I, const phi_t<T> *__restrict__ F, const AxisRec &ax,
-                                         const AxisRec &ay, int i, int j, phi_t<T> f0, T &gx, T &gy)
+template <typename T, typename R>
+__device__ __forceinline__ void grad_phi(const InstDev &I, const phi_t<T> *__restrict__ F, const R &ax,
+                                         const R &ay, int i, int j, phi_t<T> f0, T &gx, T &gy)
 {
     gx = T(ax.c1m) * phi_sub(F[cell_of(I, ax.km, j)], f0) + T(ax.c1p) * phi_sub(F[cell_of(I, ax.kp, j)], f0);
     gy = T(ay.c1m) * phi_sub(F[cell_of(I, i, ay.km)], f0) + T(ay.c1p) * phi_sub(F[cell_of(I, i, ay.kp)], f0);
@@ -166,16 +166,16 @@ __device__ __forceinline__ void grad_phi(const InstDev &I, const phi_t<T> *__res
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(TX *TY) k_macro(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles,
-                                                  const AxisRec *__restrict__ geo, Planes<T> P, int write_rho)
+                                                  const AxisRecT<T> *__restrict__ geo, Planes<T> P, int write_rho)
 {
     const int4 t = tiles[blockIdx.x];
     const InstDev &I = insts[t.x];
     const ParT<T> &Pr = par<T>(I);
-    if (P.status[t.x]) return;   // masked: non-finite instance of a batch
+    if (P.status[t.x] & ST_NONFINITE) return;   // masked: non-finite instance of a batch (a paused one still gets its macros)
     const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
     if (i >= I.nx || j >= I.ny) return;
-    const AxisRec &ax = geo[I.gx_off + i];
-    const AxisRec &ay = geo[I.gy_off + j];
+    const auto &ax = geo[I.gx_off + i];
+    const auto &ay = geo[I.gy_off + j];
     const long long c = cell_of(I, i, j);
     const long long N = P.N;
     const T cs2 = Cst<T>::cs2;
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(TX *TY) k_cell(const InstDev *__restrict__ ins
     const int4 t = tiles[blockIdx.x];
     const InstDev &I = insts[t.x];
     const ParT<T> &Pr = par<T>(I);
-    if (P.status[t.x]) return;   // masked: non-finite instance of a batch
+    if (P.status[t.x]) return;   // masked (non-finite) or paused instance of a batch
     const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
     if (i >= I.nx || j >= I.ny) return;
     const AxisRec &ax = geo[I.gx_off + i];
@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(TX *TY) k_face(const InstDev *__restrict__ ins
     const int4 t = tiles[blockIdx.x];
     const InstDev &I = insts[t.x];
     const ParT<T> &Pr = par<T>(I);
-    if (P.status[t.x]) return;   // masked: non-finite instance of a batch
+    if (P.status[t.x]) return;   // masked (non-finite) or paused instance of a batch
     const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
     if (i >= I.nx || j >= I.ny) return;
     const AxisRec &ax = geo[I.gx_off + i];

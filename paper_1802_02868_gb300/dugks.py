@@ -60,7 +60,8 @@ EXPORTS = ("dugks_create", "dugks_batch_create", "dugks_destroy", "dugks_init", 
            "dugks_launch_count", "dugks_set_timing", "dugks_kernel_times", "dugks_kernel_name",
            "dugks_kernel_bytes_per_cell", "dugks_status_str", "dugks_conservation_static",
            "dugks_autotune", "dugks_set_tile_shape", "dugks_tile_shape", "dugks_tile_shape_name",
-           "dugks_adjoint", "dugks_uniform_instances", "dugks_diagnostics", "dugks_laplace_pressure")
+           "dugks_adjoint", "dugks_uniform_instances", "dugks_diagnostics", "dugks_laplace_pressure",
+           "dugks_batch_set_paused", "dugks_batch_step_each")
 STATIC_MAX_CELLS = 16777216
 
 
@@ -107,6 +108,8 @@ def load(build_if_missing: bool = True):
     L.dugks_uniform_instances.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.dugks_diagnostics.argtypes = [vp, ctypes.POINTER(Diag_t)]
     L.dugks_laplace_pressure.argtypes = [vp, dp]
+    L.dugks_batch_set_paused.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
+    L.dugks_batch_step_each.argtypes = [vp, ctypes.POINTER(ctypes.c_long)]
     L.dugks_tile_shape_name.argtypes = [ip]
     L.dugks_tile_shape_name.restype = ctypes.c_char_p
     L.dugks_status_str.argtypes = [ip]
@@ -252,6 +255,20 @@ class Sim:
         if buf.shape[2] != self.ncells:
             raise ValueError("state has %d cells, expected %d" % (buf.shape[2], self.ncells))
         _check("dugks_load", load().dugks_load(self.h, buf.ctypes.data_as(ctypes.c_void_p), buf.nbytes))
+
+    def set_paused(self, paused):
+        """Pause (True) or resume (False) each instance (dugks_batch_set_paused)."""
+        n = len(self.meshes)
+        arr = (ctypes.c_int * n)(*[1 if p else 0 for p in paused])
+        _check("dugks_batch_set_paused", load().dugks_batch_set_paused(self.h, arr))
+        return self
+
+    def step_each(self, nsteps):
+        """Advance instance k by nsteps[k] steps (dugks_batch_step_each)."""
+        n = len(self.meshes)
+        arr = (ctypes.c_long * n)(*[int(v) for v in nsteps])
+        _check("dugks_batch_step_each", load().dugks_batch_step_each(self.h, arr))
+        return self
 
     def diagnostics(self):
         """Per-instance diagnostics (dugks_diagnostics) as dicts; one dict for a

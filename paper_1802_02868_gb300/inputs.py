@@ -169,6 +169,35 @@ def stationary_drop(n=64, radius=16.0, sigma=1e-3, width=4.0, density_ratio=10.0
     return Case("stationary_drop_%dx%d" % (n, n), mesh, prm, phi0, steps=steps)
 
 
+def droplet_sec31(radius=25.0, n=100, mobility=0.1, cfl=0.4, sigma=1e-3, width=4.0):
+    """The stationary droplet of Sec. 3.1: rhoA = 1, rhoB = 0.2, tau_f = tau_g
+    = 0.5 (nu = c_s^2 tau_f = 1/6 in both fluids), W = 4, sigma = 1e-3,
+    CFL = 0.4, an n x n periodic mesh, centred on a cell centre."""
+    beta, kappa = params_from_sigma_width(sigma, width)
+    mesh = uniform_mesh(n, n)
+    prm = Params(rhoA=1.0, rhoB=0.2, nuA=1.0 / 6.0, nuB=1.0 / 6.0, mobility=mobility, tau_g=0.5,
+                 beta=beta, kappa=kappa, cfl=cfl)
+    c = 0.5 * n + 0.5
+    phi0 = drop_field(mesh, radius, (c, c), width)
+    return Case("droplet_R%g_lam%g_cfl%g" % (radius, mobility, cfl), mesh, prm, phi0)
+
+
+def mobility_sweep(mobilities=(0.01, 0.1, 1.0), **kw):
+    """Sec. 3.1, the density profile against the mobility (one batch)."""
+    return [droplet_sec31(mobility=m, **kw) for m in mobilities]
+
+
+def cfl_sweep(cfls=(0.1, 0.2, 0.4, 0.8), mobility=0.1, **kw):
+    """Sec. 3.1, the density profile against the CFL number at lambda = 0.1
+    (one batch; each CFL has its own time step)."""
+    return [droplet_sec31(mobility=mobility, cfl=c, **kw) for c in cfls]
+
+
+def viscosity_ratio_sweep(ratios=(3.0, 10.0, 100.0, 1000.0), **kw):
+    """Sec. 3.2, the layered Poiseuille flow over viscosity ratios (one batch)."""
+    return [layered_poiseuille(nu_ratio=r, **kw) for r in ratios]
+
+
 def layered_poiseuille(nx=4, ny=256, height=256.0, nu_ratio=1.0, nuB=0.05, force=1e-6,
                        sigma=1e-3, width=4.0, mobility=0.1, cfl=0.5, eps=2.5, steps=50000):
     """Two-layer channel: walls at y=0 and y=height, fluid A below y=height/2,

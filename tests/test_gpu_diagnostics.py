@@ -38,10 +38,11 @@ def _ambiguous_volume(mesh, phi, params, eps=1e-9):
     return float(np.outer(mesh.dy, mesh.dx)[np.abs(c - 0.5) < eps].sum())
 
 
-def _compare(dg, do, Pg, Po, mesh, m, params, rtol, ptol, eps=1e-9, ufloor=1e-16):
+def _compare(dg, do, Pg, Po, mesh, m, params, rtol, ptol, eps=1e-9, ufloor=1e-16, mtol=0.0):
     """m: the oracle's moments; velocities are compared on the scale of the
-    largest velocity of the mesh."""
-    assert abs(dg["mass"] - do["mass"]) <= _ambiguous_volume(mesh, m["phi"], params, eps)
+    largest velocity of the mesh.  mtol: relative rounding of the volume sum
+    (FP32 sims sum single-precision cell volumes within a warp)."""
+    assert abs(dg["mass"] - do["mass"]) <= _ambiguous_volume(mesh, m["phi"], params, eps) + mtol * do["mass"]
     scale_u = max(np.max(np.abs(m["ux"])), np.max(np.abs(m["uy"])), 1e-300)
     for k in KEYS[1:]:
         a, b = dg[k], do[k]
@@ -95,7 +96,7 @@ def test_fp32_diagnostics_after_init_match_oracle():
         o.close()
         s = dugks.Sim(c.mesh, c.params, dugks.FP32).init(c.phi0)
         _compare(s.diagnostics(), d, s.laplace_pressure(), P, c.mesh, m, c.params, 2e-5, 2e-5, eps=1e-6,
-                 ufloor=1e-12)
+                 ufloor=1e-12, mtol=1e-6)
         s.close()
 
 
