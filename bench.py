@@ -44,11 +44,13 @@ FLOP_PER_CELL_UPDATE = 2127.0
 # lanes x 2 flop x 2.07 GHz, and 152 SMs x 2 DFMA/cycle x 2 flop x 2.07 GHz.
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# DRAM bytes per cell of one k_step launch from the ncu capture summarised in
-# profiles/k_step_fp32_drop2048.md (dram__bytes_read.sum + dram__bytes_write.sum
-# over 4,194,304 cells), valid only for the kernel sources it was taken on.
-TRAFFIC_SOURCES_SHA = "3b949e17ba0f449a"
-TRAFFIC_BYTES_PER_CELL_FP32 = (336.806400e6 + 297.182464e6) / 4194304
+# DRAM bytes per cell of one k_step launch (the 32x8 tile, uniform periodic
+# path) from an ncu capture of a 2048 x 2048 periodic drop
+# (dram__bytes_read.sum + dram__bytes_write.sum over 4,194,304 cells), valid
+# only for the kernel sources and the tile shape it was taken on.
+TRAFFIC_SOURCES_SHA = "f7e283ceb385259b"
+TRAFFIC_SHAPE = "32x8"
+TRAFFIC_BYTES_PER_CELL_FP32 = (336.531968e6 + 298.570496e6) / 4194304
 
 
 def kernel_sources_sha():
@@ -340,7 +342,7 @@ def main():
     # pinned host buffers for the end-to-end leg
     phi_h = torch.from_numpy(np.concatenate([c.phi0.reshape(-1) for c in cases])).pin_memory()
     sim.init(phi_h.numpy())
-    tuned = sim.autotune(steps=3) if not args.no_autotune else (0, dugks.tile_shape_name(0), None)
+    tuned = sim.autotune(steps=10) if not args.no_autotune else (0, dugks.tile_shape_name(0), None)
     for _ in range(args.warmup):
         sim.step(1)
     torch.cuda.synchronize()
@@ -412,7 +414,8 @@ def main():
     tflops = FLOP_PER_CELL_UPDATE * ncells / avg_s / 1e12
     peak_alu = PEAK_FP32_TFLOPS if prec == dugks.FP32 else PEAK_FP64_TFLOPS
     traffic = None
-    if kname == "k_step" and prec == dugks.FP32 and kernel_sources_sha() == TRAFFIC_SOURCES_SHA:
+    if kname == "k_step" and prec == dugks.FP32 and kernel_sources_sha() == TRAFFIC_SOURCES_SHA \
+            and tuned[1] == TRAFFIC_SHAPE:
         traffic = TRAFFIC_BYTES_PER_CELL_FP32 * ncells
     roof = {"bound": "alu", "kernel": kname, "achieved": tflops, "peak": peak_alu, "unit": "TFLOP/s",
             "frac": tflops / peak_alu, "peak_source": "unit counts x 2.07 GHz max SM clock (%s)" % (
