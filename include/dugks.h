@@ -171,13 +171,16 @@ const char *dugks_kernel_name(int k);
    accounting), for this sim's precision. */
 int dugks_kernel_bytes_per_cell(const dugks_sim *sim, int k, double *bytes);
 
-/* Tile shapes of the fused step: 0 = 32x8 cells (the default), 1 = 16x16,
-   2 = 32x12.  dugks_autotune times every shape on the sim's current state for
+/* Tile shapes of the fused step, each a tile of cells per thread block:
+   0 = 32x8 cells on 256 threads (the default), 1 = 32x4 on 128 threads,
+   2 = 32x12 on 384 threads, 3 = 32x8 on 352 threads with the face fluxes in
+   their own shared memory (two blocks per SM).  Every shape computes the same
+   result bit for bit.  dugks_autotune times every shape on the sim's current state for
    `steps` steps each (CUDA events on the sim's stream), restores the state and
    the per-instance status after each trial, keeps the fastest shape and
    returns its index and time per step.  It allocates a temporary snapshot of
    the state (cudaMalloc) for the duration of the call and synchronises. */
-#define DUGKS_NUM_TILE_SHAPES 5
+#define DUGKS_NUM_TILE_SHAPES 4
 int dugks_autotune(dugks_sim *sim, int steps, int *chosen, double *ms_per_step);
 int dugks_set_tile_shape(dugks_sim *sim, int shape);
 int dugks_tile_shape(const dugks_sim *sim, int *shape, int *bx, int *by);

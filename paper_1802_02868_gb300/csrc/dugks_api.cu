@@ -91,10 +91,9 @@ struct ShapeDesc {
     const char *name;
 };
 const ShapeDesc kShapes[DUGKS_NUM_TILE_SHAPES] = {{32, 8, 256, 0, "32x8"},
-                                                  {16, 16, 256, 0, "16x16"},
+                                                  {32, 4, 128, 0, "32x4/128"},
                                                   {32, 12, 384, 0, "32x12"},
-                                                  {32, 8, 352, 1, "32x8/352 sep"},
-                                                  {32, 8, 384, 1, "32x8/384 sep"}};
+                                                  {32, 8, 352, 1, "32x8/352 sep"}};
 
 const char *kNames[K_COUNT] = {"k_mu", "k_macro", "k_cell", "k_face", "k_init", "k_reduce", "k_step", "k_diag"};
 
@@ -238,7 +237,7 @@ void harvest_events(dugks_sim *s)
 // Resident CTAs per SM that the registers of a fused-step instantiation are
 // sized for (shared memory allows the same count).
 template <typename T, int NT, bool SEP>
-constexpr int fused_minb() { return sizeof(T) == 8 ? 1 : (SEP || NT > 256 ? 2 : 3); }
+constexpr int fused_minb() { return sizeof(T) == 8 ? 1 : (SEP || NT > 256 ? 2 : NT <= 128 ? 4 : 3); }
 
 template <typename T, int BX, int BY, int NT, bool SEP>
 int prepare_shape()
@@ -290,10 +289,9 @@ int prepare_fused(dugks_sim *s)
     int rc = ensure_tiles(s, s->shape);
     if (rc) return rc;
     switch (s->shape) {
-    case 1: return prepare_shape<T, 16, 16, 256, false>();
+    case 1: return prepare_shape<T, 32, 4, 128, false>();
     case 2: return prepare_shape<T, 32, 12, 384, false>();
     case 3: return prepare_shape<T, 32, 8, 352, true>();
-    case 4: return prepare_shape<T, 32, 8, 384, true>();
     default: return prepare_shape<T, 32, 8, 256, false>();
     }
 }
@@ -334,10 +332,9 @@ template <typename T>
 void enqueue_fused(dugks_sim *s, const StepIO<T> &io, cudaStream_t st)
 {
     switch (s->shape) {
-    case 1: enqueue_shape<T, 16, 16, 256, false>(s, 1, io, st); break;
+    case 1: enqueue_shape<T, 32, 4, 128, false>(s, 1, io, st); break;
     case 2: enqueue_shape<T, 32, 12, 384, false>(s, 2, io, st); break;
     case 3: enqueue_shape<T, 32, 8, 352, true>(s, 3, io, st); break;
-    case 4: enqueue_shape<T, 32, 8, 384, true>(s, 4, io, st); break;
     default: enqueue_shape<T, 32, 8, 256, false>(s, 0, io, st); break;
     }
 }
