@@ -313,6 +313,7 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tile-shape", type=int, default=None, help="use this fused-step shape instead of autotuning")
     ap.add_argument("--adjoint", action="store_true", help="time the adjoint workload instead")
     ap.add_argument("--adjoint-steps", type=int, default=4000)
     args = ap.parse_args()
@@ -342,7 +343,11 @@ def main():
     # pinned host buffers for the end-to-end leg
     phi_h = torch.from_numpy(np.concatenate([c.phi0.reshape(-1) for c in cases])).pin_memory()
     sim.init(phi_h.numpy())
-    tuned = sim.autotune(steps=10) if not args.no_autotune else (0, dugks.tile_shape_name(0), None)
+    if args.tile_shape is not None:
+        sim.set_tile_shape(args.tile_shape)
+        tuned = (args.tile_shape, dugks.tile_shape_name(args.tile_shape), None)
+    else:
+        tuned = sim.autotune(steps=10) if not args.no_autotune else (0, dugks.tile_shape_name(0), None)
     for _ in range(args.warmup):
         sim.step(1)
     torch.cuda.synchronize()

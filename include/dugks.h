@@ -180,7 +180,7 @@ int dugks_kernel_bytes_per_cell(const dugks_sim *sim, int k, double *bytes);
    the per-instance status after each trial, keeps the fastest shape and
    returns its index and time per step.  It allocates a temporary snapshot of
    the state (cudaMalloc) for the duration of the call and synchronises. */
-#define DUGKS_NUM_TILE_SHAPES 4
+#define DUGKS_NUM_TILE_SHAPES 7
 int dugks_autotune(dugks_sim *sim, int steps, int *chosen, double *ms_per_step);
 int dugks_set_tile_shape(dugks_sim *sim, int shape);
 int dugks_tile_shape(const dugks_sim *sim, int *shape, int *bx, int *by);

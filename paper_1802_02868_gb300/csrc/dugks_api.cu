@@ -16,6 +16,7 @@
 #include "dugks_common.cuh"
 #include "dugks_kernels.cuh"
 #include "dugks_fused.cuh"
+#include "dugks_strip.cuh"
 #include "dugks_adjoint.cuh"
 #include "dugks_diag.cuh"
 
@@ -87,13 +88,16 @@ namespace {
 // tile per thread block of NT threads; "sep" gives the face fluxes their own
 // shared memory (two blocks per SM instead of three in FP32).
 struct ShapeDesc {
-    int bx, by, nt, sep;
+    int bx, by, nt, sep, nb;   // nb > 0: a strip of up to nb blocks per thread block (k_strip)
     const char *name;
 };
-const ShapeDesc kShapes[DUGKS_NUM_TILE_SHAPES] = {{32, 8, 256, 0, "32x8"},
-                                                  {32, 4, 128, 0, "32x4/128"},
-                                                  {32, 12, 384, 0, "32x12"},
-                                                  {32, 8, 352, 1, "32x8/352 sep"}};
+const ShapeDesc kShapes[DUGKS_NUM_TILE_SHAPES] = {{32, 8, 256, 0, 0, "32x8"},
+                                                  {32, 4, 128, 0, 0, "32x4/128"},
+                                                  {32, 12, 384, 0, 0, "32x12"},
+                                                  {32, 8, 352, 1, 0, "32x8/352 sep"},
+                                                  {32, 8, 288, 0, 8, "32x8 strip8/288"},
+                                                  {32, 8, 288, 0, 16, "32x8 strip16/288"},
+                                                  {32, 8, 288, 0, 32, "32x8 strip32/288"}};
 
 const char *kNames[K_COUNT] = {"k_mu", "k_macro", "k_cell", "k_face", "k_init", "k_reduce", "k_step", "k_diag"};
 
@@ -237,7 +241,7 @@ void harvest_events(dugks_sim *s)
 // Resident CTAs per SM that the registers of a fused-step instantiation are
 // sized for (shared memory allows the same count).
 template <typename T, int NT, bool SEP>
-constexpr int fused_minb() { return sizeof(T) == 8 ? 1 : (SEP || NT > 256 ? 2 : NT <= 128 ? 4 : 3); }
+constexpr int fused_minb() { return sizeof(T) == 8 ? 1 : (SEP || NT > 288 ? 2 : NT <= 128 ? 4 : 3); }
 
 template <typename T, int BX, int BY, int NT, bool SEP>
 int prepare_shape()
@@ -257,18 +261,39 @@ int prepare_shape()
     return DUGKS_OK;
 }
 
+template <typename T, int BX, int BY, int NT>
+int prepare_strip()
+{
+    using SL = StripLayout<T, BX, BY>;
+    constexpr int MB = fused_minb<T, NT, false>();
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_strip<T, BX, BY, NT, MB, false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SL::bytes);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_strip<T, BX, BY, NT, MB, true>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SL::bytes);
+        if (e != cudaSuccess) return cuda_status(e);
+        attr_set = true;
+    }
+    return DUGKS_OK;
+}
+
 // fused-step tile table of shape k: the uniform periodic instances' tiles first
 int ensure_tiles(dugks_sim *s, int k)
 {
     if (s->d_tiles_s[k]) return DUGKS_OK;
     std::vector<int4> tiles;
-    const int bx = kShapes[k].bx, by = kShapes[k].by;
+    // {instance, first column, first row, blocks of a strip (0 for a tile)}
+    const int bx = kShapes[k].bx, by = kShapes[k].by, nb = kShapes[k].nb;
+    const int span = nb ? nb * by : by;
     for (int pass = 0; pass < 2; pass++) {
         for (int i = 0; i < s->n_inst; i++) {
             const InstDev &I = s->h_inst[i];
             if ((pass == 0) != (s->use_uni && I.uni)) continue;
-            for (int ty = 0; ty < I.ny; ty += by)
-                for (int tx = 0; tx < I.nx; tx += bx) tiles.push_back(make_int4(i, tx, ty, 0));
+            for (int ty = 0; ty < I.ny; ty += span)
+                for (int tx = 0; tx < I.nx; tx += bx)
+                    tiles.push_back(make_int4(i, tx, ty, nb ? std::min(nb, (I.ny - ty + by - 1) / by) : 0));
         }
         if (pass == 0) s->n_uni_s[k] = (int)tiles.size();
     }
@@ -292,6 +317,9 @@ int prepare_fused(dugks_sim *s)
     case 1: return prepare_shape<T, 32, 4, 128, false>();
     case 2: return prepare_shape<T, 32, 12, 384, false>();
     case 3: return prepare_shape<T, 32, 8, 352, true>();
+    case 4:
+    case 5:
+    case 6: return prepare_strip<T, 32, 8, 288>();
     default: return prepare_shape<T, 32, 8, 256, false>();
     }
 }
@@ -317,6 +345,17 @@ int fused_launches(const dugks_sim *s)
     return (s->n_uni_s[k] > 0) + (s->n_tiles_s[k] > s->n_uni_s[k]);
 }
 
+template <typename T, int BX, int BY, int NT>
+void enqueue_strip(dugks_sim *s, int k, const StepIO<T> &io, cudaStream_t st)
+{
+    using SL = StripLayout<T, BX, BY>;
+    constexpr int MB = fused_minb<T, NT, false>();
+    const int nu = s->n_uni_s[k], ng = s->n_tiles_s[k] - nu;
+    const AxisRecT<T> *geo = (const AxisRecT<T> *)s->d_geoT;
+    if (nu > 0) k_strip<T, BX, BY, NT, MB, true><<<(unsigned)nu, NT, SL::bytes, st>>>(s->d_inst, s->d_tiles_s[k], geo, io);
+    if (ng > 0) k_strip<T, BX, BY, NT, MB, false><<<(unsigned)ng, NT, SL::bytes, st>>>(s->d_inst, s->d_tiles_s[k] + nu, geo, io);
+}
+
 template <typename T, int BX, int BY, int NT, bool SEP>
 void enqueue_shape(dugks_sim *s, int k, const StepIO<T> &io, cudaStream_t st)
 {
@@ -335,6 +374,9 @@ void enqueue_fused(dugks_sim *s, const StepIO<T> &io, cudaStream_t st)
     case 1: enqueue_shape<T, 32, 4, 128, false>(s, 1, io, st); break;
     case 2: enqueue_shape<T, 32, 12, 384, false>(s, 2, io, st); break;
     case 3: enqueue_shape<T, 32, 8, 352, true>(s, 3, io, st); break;
+    case 4:
+    case 5:
+    case 6: enqueue_strip<T, 32, 8, 288>(s, s->shape, io, st); break;
     default: enqueue_shape<T, 32, 8, 256, false>(s, 0, io, st); break;
     }
 }
@@ -1223,7 +1265,7 @@ int dugks_tile_shape(const dugks_sim *s, int *shape, int *bx, int *by)
     if (!s) return DUGKS_ERR_ARG;
     if (shape) *shape = s->shape;
     if (bx) *bx = kShapes[s->shape].bx;
-    if (by) *by = kShapes[s->shape].by;
+    if (by) *by = kShapes[s->shape].by * std::max(kShapes[s->shape].nb, 1);
     return DUGKS_OK;
 }
 

@@ -1,0 +1,404 @@
+// dugks_strip.cuh -- the DUGKS step (Sec. 2.2, steps 2-7) for a strip of
+// blocks: a thread block owns BX columns and marches up a run of blocks of BY
+// rows (the strip length comes from the strip table), bottom to top.
+//
+// The per-block regions and phases are those of k_step (dugks_fused.cuh):
+// phi on a 4-cell ring, mu on 3, p on 2, bar-plus and the face aux fields on
+// 1, then the faces and the update.  Consecutive blocks share the top rows of
+// these rings, so each block computes only its BY new rows of every region and
+// shifts the shared rows, and the geometry of the rows, down afterwards; the y
+// faces between two blocks are computed once and carried over.  A prologue
+// computes the bottom rows of the first block's rings.  Shared memory does not
+// grow with the strip length.  The thread count NT is chosen so that the new
+// rows of a phase fill whole passes of the threads (with BX = 32, BY = 8 and
+// 288 threads: p 288 items, bar-plus 272, faces 520 in two passes).
+#pragma once
+#include "dugks_fused.cuh"
+
+namespace dugks {
+
+template <typename T, int BX, int BY>
+struct StripLayout {
+    using L = FusedLayout<T, BX, BY, false>;
+    static_assert(BY >= 8, "the shifted ring rows must not overlap the new rows");
+    static constexpr int NFY = BX * BY;                   // y faces per block (the bottom row is carried)
+    static constexpr int NFT = L::NFX + NFY;
+    static constexpr int FROWS = BY + 1, GROWS = BY;      // staged tilde rows of a block (f: 1..BY+1, g: 1..BY)
+    static constexpr size_t al(size_t v) { return (v + 15) / 16 * 16; }
+    static constexpr size_t o_un = L::o_un;               // after the R1 planes
+    static constexpr size_t st_f = sizeof(T) * Q * FROWS * L::W2;
+    static constexpr size_t st_g = sizeof(T) * Q * GROWS * L::W1;
+    static constexpr size_t st_flux = sizeof(pair_t<T>) * 6 * NFT;
+    static constexpr size_t un = (st_f + st_g > st_flux) ? st_f + st_g : st_flux;
+    static constexpr size_t o_keep = al(o_un + un);       // carried y-face row [6][BX] pairs
+    static constexpr size_t bytes = al(o_keep + sizeof(pair_t<T>) * 6 * BX);
+};
+
+template <typename T, int BX, int BY, int NT, int MINB, bool UNI>
+__global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ insts, const int4 *__restrict__ chunks,
+                                                    const AxisRecT<T> *__restrict__ geo, StepIO<T> io)
+{
+    static_assert(NT % 32 == 0 && NT >= BX * BY, "thread count");
+    using SL = StripLayout<T, BX, BY>;
+    using L = typename SL::L;
+    using TL = Tile<T, BX, BY, UNI, false>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    TL S(smem);
+    T *stf = (T *)(smem + SL::o_un);                      // staged tilde f [Q][FROWS][W2]
+    T *stg = stf + Q * SL::FROWS * L::W2;                 // staged tilde g [Q][GROWS][W1]
+    pair_t<T> *flux = (pair_t<T> *)(smem + SL::o_un);    // [6][NFT], reuses the staging bytes
+    pair_t<T> *keep = (pair_t<T> *)(smem + SL::o_keep);  // [6][BX]: the bottom y faces of the block
+    const int4 t = chunks[blockIdx.x];
+    const InstDev &I = insts[t.x];
+    const ParT<T> &Pr = par<T>(I);
+    const int i0 = t.y, j0 = t.z, nblk = t.w;
+    const int tid = threadIdx.x;
+    const long long N = io.N;
+    auto cell = [&](int gi, int gj) -> long long { return I.cell0 + (long long)gj * I.nxp + gi; };
+    {
+        const int st = io.status[t.x];
+        if (st & ST_NONFINITE) return;   // masked: non-finite instance of a batch
+        if (st & ST_PAUSED) {            // paused: the state passes to the other buffer unchanged
+            for (int r = tid; r < BX * BY * nblk; r += NT) {
+                const int gi = i0 + r % BX, gj = j0 + r / BX;
+                if (gi >= I.nx || gj >= I.ny) continue;
+                const long long c = cell(gi, gj);
+#pragma unroll
+                for (int q = 0; q < Q; q++) {
+                    io.f_out[q * N + c] = io.f_in[q * N + c];
+                    io.g_out[q * N + c] = io.g_in[q * N + c];
+                }
+                io.phi_out[c] = io.phi_in[c];
+            }
+            return;
+        }
+    }
+    const T cs2 = Cst<T>::cs2;
+    const T hdt = T(0.5) * Pr.dt, dt = Pr.dt, h = Pr.h, tg = Pr.tau_g;
+    const T rg = fdiv(T(1), T(2) * tg + dt);
+    const T ag = (T(2) * tg - h) * rg, bg = T(3) * h * rg, cg = T(3) * tg * h * rg;
+    // global index of a column (x) or of row y of block b (wrapped on a periodic
+    // axis, -1 outside the domain)
+    auto gwrap = [&](bool isx, int g) -> int {
+        const int n = isx ? I.nx : I.ny;
+        if ((isx ? I.bcx : I.bcy) == 0) {
+            while (g < 0) g += n;
+            while (g >= n) g -= n;
+            return g;
+        }
+        return (g < 0 || g >= n) ? -1 : g;
+    };
+    auto grow = [&](int b, int y) -> int { return gwrap(false, j0 + b * BY + y); };
+    // geometry entry r: global index, record and flags (on a uniform periodic
+    // instance only position 0 of each axis carries the record)
+    auto set_geo = [&](int r, bool isx, int pos, int g) {
+        S.gg[r] = g;
+        if (UNI && pos != 0) return;
+        T v[11];
+        int fl = 0;
+        if (g >= 0) {
+            const AxisRecT<T> &R = geo[(isx ? I.gx_off : I.gy_off) + g];
+            v[0] = R.c1m; v[1] = R.c1p; v[2] = R.c2m; v[3] = R.c2p;
+            v[4] = R.e1m; v[5] = R.e10; v[6] = R.e1p;
+            v[7] = R.wL; v[8] = R.wR; v[9] = R.invd; v[10] = R.d;
+            fl = (R.km == g ? 0 : 1) | (R.kp == g ? 0 : 2) | (R.lo_wall ? 4 : 0) | (R.hi_wall ? 8 : 0);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 11; k++) v[k] = T(0);
+        }
+#pragma unroll
+        for (int k = 0; k < 11; k++) S.ga[k * L::NG + r] = v[k];
+        S.gf[r] = fl;
+    };
+
+    // ---- geometry of the columns and of the first block's rows -4..3
+    for (int r = tid; r < L::W4 + 8; r += NT) {
+        if (r < L::W4) set_geo(r, true, r - 4, gwrap(true, i0 + r - 4));
+        else set_geo(r, false, r - L::W4 - 4, grow(0, r - L::W4 - 4));
+    }
+    __syncthreads();
+
+    // rows of block b: phi [ph0, ph1) into the phi ring, tilde f rows [fr0, fr1)
+    // and tilde g rows [gr0, gr1) into the staging area (zero outside the
+    // domain), and the geometry of the rows [4, BY + 4) that are new to it
+    auto load_rows = [&](int b, int ph0, int ph1, int fr0, int fr1, int gr0, int gr1) {
+        if (b >= 0)
+            for (int r = tid; r < BY; r += NT) set_geo(L::W4 + 8 + r, false, 4 + r, grow(b, 4 + r));
+        const int bb = b < 0 ? 0 : b;
+        for (int r = tid; r < (ph1 - ph0) * L::W4; r += NT) {
+            const int x = r % L::W4 - 4, y = ph0 + r / L::W4;
+            const int gi = S.gidx(0, x), gj = grow(bb, y);
+            if (UNI || (gi >= 0 && gj >= 0)) {
+                cp_async<sizeof(phi_t<T>)>(S.phi + TL::i4(x, y), io.phi_in + cell(gi, gj));
+            } else {
+                phi_t<T> z;
+                phi_from_zero(z);
+                S.phi[TL::i4(x, y)] = z;
+            }
+        }
+        for (int r = tid; r < (fr1 - fr0) * L::W2; r += NT) {
+            const int x = r % L::W2 - 2, yy = r / L::W2;
+            const int gi = S.gidx(0, x), gj = grow(bb, fr0 + yy);
+            T *d = stf + yy * L::W2 + (x + 2);
+            if (UNI || (gi >= 0 && gj >= 0)) {
+                const long long c = cell(gi, gj);
+#pragma unroll
+                for (int q = 0; q < Q; q++) cp_async<sizeof(T)>(d + q * SL::FROWS * L::W2, io.f_in + q * N + c);
+            } else {
+#pragma unroll
+                for (int q = 0; q < Q; q++) d[q * SL::FROWS * L::W2] = T(0);
+            }
+        }
+        for (int r = tid; r < (gr1 - gr0) * L::W1; r += NT) {
+            const int x = r % L::W1 - 1, yy = r / L::W1;
+            const int gi = S.gidx(0, x), gj = grow(bb, gr0 + yy);
+            T *d = stg + yy * L::W1 + (x + 1);
+            if (UNI || (gi >= 0 && gj >= 0)) {
+                const long long c = cell(gi, gj);
+#pragma unroll
+                for (int q = 0; q < Q; q++) cp_async<sizeof(T)>(d + q * SL::GROWS * L::W1, io.g_in + q * N + c);
+            } else {
+#pragma unroll
+                for (int q = 0; q < Q; q++) d[q * SL::GROWS * L::W1] = T(0);
+            }
+        }
+        cp_commit();
+        cp_wait<0>();
+        __syncthreads();
+    };
+
+    // mu on R3 rows [y0, y1) (Eq. chemicalpotential)
+    auto mu_rows = [&](int y0, int y1) {
+        for (int r = tid; r < (y1 - y0) * L::W3; r += NT) {
+            const int x = r % L::W3 - 3, y = y0 + r / L::W3;
+            T mu = 0;
+            if (S.ok(0, x) && S.ok(1, y)) {
+                const phi_t<T> p0 = S.phi[TL::i4(x, y)];
+                const T lap = (S.c(2, 0, x) * phi_sub(S.phi[TL::i4(x + S.om(0, x), y)], p0)
+                             + S.c(3, 0, x) * phi_sub(S.phi[TL::i4(x + S.op(0, x), y)], p0))
+                            + (S.c(2, 1, y) * phi_sub(S.phi[TL::i4(x, y + S.om(1, y))], p0)
+                             + S.c(3, 1, y) * phi_sub(S.phi[TL::i4(x, y + S.op(1, y))], p0));
+                const T dpsi = T(4) * Pr.beta * phi_subc(p0, I.cA) * phi_subc(p0, I.cB) * phi_subc(p0, I.cM);
+                mu = dpsi - Pr.kappa * lap;
+            }
+            S.mu[TL::i3(x, y)] = mu;
+        }
+        __syncthreads();
+    };
+
+    // p on R2 rows [y0, y1) (Eqs. u, P); tilde f staged from row fr0
+    auto p_rows = [&](int y0, int y1, int fr0) {
+        for (int r = tid; r < (y1 - y0) * L::W2; r += NT) {
+            const int x = r % L::W2 - 2, y = y0 + r / L::W2;
+            T vp = 0;
+            if (S.ok(0, x) && S.ok(1, y)) {
+                const T m0 = S.mu[TL::i3(x, y)];
+                const T mxm = S.mu[TL::i3(x + S.om(0, x), y)] - m0, mxp = S.mu[TL::i3(x + S.op(0, x), y)] - m0;
+                const T mym = S.mu[TL::i3(x, y + S.om(1, y))] - m0, myp = S.mu[TL::i3(x, y + S.op(1, y))] - m0;
+                const T gmx = S.c(0, 0, x) * mxm + S.c(1, 0, x) * mxp;
+                const T gmy = S.c(0, 1, y) * mym + S.c(1, 1, y) * myp;
+                const T lmu = (S.c(2, 0, x) * mxm + S.c(3, 0, x) * mxp) + (S.c(2, 1, y) * mym + S.c(3, 1, y) * myp);
+                const phi_t<T> p0 = S.phi[TL::i4(x, y)];
+                const T gfx = S.c(0, 0, x) * phi_sub(S.phi[TL::i4(x + S.om(0, x), y)], p0)
+                            + S.c(1, 0, x) * phi_sub(S.phi[TL::i4(x + S.op(0, x), y)], p0);
+                const T gfy = S.c(0, 1, y) * phi_sub(S.phi[TL::i4(x, y + S.om(1, y))], p0)
+                            + S.c(1, 1, y) * phi_sub(S.phi[TL::i4(x, y + S.op(1, y))], p0);
+                const T phi = T(phi_val(p0));
+                const T rho = rho_of<T>(I, phi);
+                const T Fx = -phi * gmx + (rho - Pr.rho_ref) * Pr.gxa;
+                const T Fy = -phi * gmy + (rho - Pr.rho_ref) * Pr.gya;
+                const T *fr = stf + (y - fr0) * L::W2 + (x + 2);
+                T sf = 0, mx = 0, my = 0;
+#pragma unroll
+                for (int q = 0; q < Q; q++) {
+                    const T v = fr[q * SL::FROWS * L::W2];
+                    sf += v;
+                    if (cx(q)) mx += T(cx(q)) * v;
+                    if (cy(q)) my += T(cy(q)) * v;
+                }
+                const T irho = fdiv(T(1), rho);
+                const T ux = (T(3) * mx + hdt * Fx) * irho;
+                const T uy = (T(3) * my + hdt * Fy) * irho;
+                vp = sf + hdt * cs2 * (ux * Pr.drho * gfx + uy * Pr.drho * gfy - Pr.gamma * rho * Pr.lambda * lmu);
+            }
+            S.p[TL::i2(x, y)] = vp;
+        }
+        __syncthreads();
+    };
+
+    // grad p, the face aux fields and bar-plus on R1 rows [y0, y1) (Eq. relations1);
+    // tilde f staged from row fr0, tilde g from row gr0
+    auto r1_rows = [&](int y0, int y1, int fr0, int gr0) {
+        for (int r = tid; r < (y1 - y0) * L::W1; r += NT) {
+            const int x = r % L::W1 - 1, y = y0 + r / L::W1;
+            const int k1 = TL::i1(x, y);
+            if (!S.ok(0, x) || !S.ok(1, y)) {
+                S.gmx[k1] = 0; S.gmy[k1] = 0; S.lmu[k1] = 0; S.gfx[k1] = 0; S.gfy[k1] = 0; S.gpx[k1] = 0; S.gpy[k1] = 0;
+#pragma unroll
+                for (int q = 0; q < Q; q++) S.bp[q * L::A1 + k1] = pr(T(0));
+                continue;
+            }
+            const T p0 = S.p[TL::i2(x, y)];
+            const T gpx = S.c(0, 0, x) * (S.p[TL::i2(x + S.om(0, x), y)] - p0) + S.c(1, 0, x) * (S.p[TL::i2(x + S.op(0, x), y)] - p0);
+            const T gpy = S.c(0, 1, y) * (S.p[TL::i2(x, y + S.om(1, y))] - p0) + S.c(1, 1, y) * (S.p[TL::i2(x, y + S.op(1, y))] - p0);
+            const T m0 = S.mu[TL::i3(x, y)];
+            const T mxm = S.mu[TL::i3(x + S.om(0, x), y)] - m0, mxp = S.mu[TL::i3(x + S.op(0, x), y)] - m0;
+            const T mym = S.mu[TL::i3(x, y + S.om(1, y))] - m0, myp = S.mu[TL::i3(x, y + S.op(1, y))] - m0;
+            const T gmx = S.c(0, 0, x) * mxm + S.c(1, 0, x) * mxp;
+            const T gmy = S.c(0, 1, y) * mym + S.c(1, 1, y) * myp;
+            const T lmu = (S.c(2, 0, x) * mxm + S.c(3, 0, x) * mxp) + (S.c(2, 1, y) * mym + S.c(3, 1, y) * myp);
+            const phi_t<T> ph0 = S.phi[TL::i4(x, y)];
+            const T gfx = S.c(0, 0, x) * phi_sub(S.phi[TL::i4(x + S.om(0, x), y)], ph0)
+                        + S.c(1, 0, x) * phi_sub(S.phi[TL::i4(x + S.op(0, x), y)], ph0);
+            const T gfy = S.c(0, 1, y) * phi_sub(S.phi[TL::i4(x, y + S.om(1, y))], ph0)
+                        + S.c(1, 1, y) * phi_sub(S.phi[TL::i4(x, y + S.op(1, y))], ph0);
+            S.gmx[k1] = gmx; S.gmy[k1] = gmy; S.lmu[k1] = lmu; S.gfx[k1] = gfx; S.gfy[k1] = gfy; S.gpx[k1] = gpx; S.gpy[k1] = gpy;
+            const T *fr = stf + (y - fr0) * L::W2 + (x + 2);
+            const T *gr = stg + (y - gr0) * L::W1 + (x + 1);
+            T fv[Q];
+            T mx = 0, my = 0;
+#pragma unroll
+            for (int q = 0; q < Q; q++) {
+                fv[q] = fr[q * SL::FROWS * L::W2];
+                if (cx(q)) mx += T(cx(q)) * fv[q];
+                if (cy(q)) my += T(cy(q)) * fv[q];
+            }
+            Pt<T> s;
+            s.phi = T(phi_val(ph0));
+            s.rho = rho_of<T>(I, s.phi);
+            s.Fx = -s.phi * gmx + (s.rho - Pr.rho_ref) * Pr.gxa;
+            s.Fy = -s.phi * gmy + (s.rho - Pr.rho_ref) * Pr.gya;
+            const T irho = fdiv(T(1), s.rho);
+            s.ux = (T(3) * mx + hdt * s.Fx) * irho;
+            s.uy = (T(3) * my + hdt * s.Fy) * irho;
+            s.p = p0;
+            s.mu = m0;
+            s.lapmu = lmu;
+            s.grx = Pr.drho * gfx;
+            s.gry = Pr.drho * gfy;
+            s.gpx = gpx;
+            s.gpy = gpy;
+            const T tf = tauf_of<T>(I, s.phi, s.rho);
+            const T rf = fdiv(T(1), T(2) * tf + dt);
+            const T af = (T(2) * tf - h) * rf, bf = T(3) * h * rf, cf = T(3) * tf * h * rf;
+            const PtInv<T> v = pt_inv<T>(I, s);
+#pragma unroll
+            for (int q = 0; q < Q; q++) {
+                T feq, geq, Ff, Fg;
+                eq_src<T>(s, v, q, feq, geq, Ff, Fg);
+                S.bp[q * L::A1 + k1] = pfma(pr(af, ag), pr(fv[q], gr[q * SL::GROWS * L::W1]),
+                                            pfma(pr(bf, bg), pr(feq, geq), pmul(pr(cf, cg), pr(Ff, Fg))));
+            }
+        }
+        __syncthreads();
+    };
+
+    // ---- prologue: the bottom rows of the first block's rings
+    load_rows(-1, -4, 4, -2, 2, -1, 1);
+    mu_rows(-3, 3);
+    p_rows(-2, 2, -2);
+    r1_rows(-1, 1, -2, -1);
+
+    const int x = tid % BX, y = tid / BX;
+    for (int b = 0; b < nblk; b++) {
+        // ---- the new rows of every region
+        load_rows(b, 4, BY + 4, 1, BY + 2, 1, BY + 1);
+        mu_rows(3, BY + 3);
+        p_rows(2, BY + 2, 1);
+        r1_rows(1, BY + 1, 1, 1);
+        // ---- faces: x faces of the block rows and y faces 0|1 .. BY-1|BY; the
+        // first block also forms its bottom faces -1|0 (a wall face there
+        // differences bar-plus up to row 1); later blocks carry them over
+        const int nf = SL::NFT + (b == 0 ? BX : 0);
+        for (int k = tid; k < nf; k += NT) {
+            pair_t<T> F2o[6];
+            if (k < L::NFX) tile_face<T, 0, UNI>(I, S, k % (BX + 1) - 1, k / (BX + 1), F2o);
+            else if (k < SL::NFT) tile_face<T, 1, UNI>(I, S, (k - L::NFX) % BX, (k - L::NFX) / BX, F2o);
+            else tile_face<T, 1, UNI>(I, S, k - SL::NFT, -1, F2o);
+            pair_t<T> *dst = k < SL::NFT ? flux + k : keep + (k - SL::NFT);
+            const int stride = k < SL::NFT ? SL::NFT : BX;
+#pragma unroll
+            for (int m = 0; m < 6; m++) dst[m * stride] = F2o[m];
+        }
+        __syncthreads();
+        // ---- update of the block's cell (Eqs. relations2, updatef)
+        const int gi = i0 + x, gj = j0 + b * BY + y;
+        if (tid < BX * BY && gi < I.nx && gj < I.ny) {
+            pair_t<T> J[Q];
+#pragma unroll
+            for (int q = 0; q < Q; q++) J[q] = pr(T(0));
+            const int kw = y * (BX + 1) + x, ke = kw + 1;
+            const int kn = L::NFX + y * BX + x;               // face between rows y and y + 1
+#pragma unroll
+            for (int m = 0; m < 6; m++) {
+                const int qx = xset(m), qy = yset(m);
+                const pair_t<T> south = (y == 0) ? keep[m * BX + x] : flux[m * SL::NFT + kn - BX];
+                J[qx] = padd(J[qx], psub(flux[m * SL::NFT + ke], flux[m * SL::NFT + kw]));
+                J[qy] = padd(J[qy], psub(flux[m * SL::NFT + kn], south));
+            }
+            const long long c = cell(gi, gj);
+            const int r1 = TL::i1(x, y);
+            const T dtv = dt / (S.c(10, 0, x) * S.c(10, 1, y));
+            pair_t<T> nw[Q];
+#pragma unroll
+            for (int q = 0; q < Q; q++)
+                nw[q] = pfma(pr(T(4.0 / 3.0)), S.bp[q * L::A1 + r1],
+                             pfma(pr(T(-1.0 / 3.0)), pr(io.f_in[q * N + c], io.g_in[q * N + c]), pmul(pr(-dtv), J[q])));
+            bool finite = true;
+            if constexpr (sizeof(T) == sizeof(double)) {
+                T phi = 0;
+#pragma unroll
+                for (int q = 0; q < Q; q++) {
+                    io.f_out[q * N + c] = nw[q].x;
+                    io.g_out[q * N + c] = nw[q].y;
+                    phi += nw[q].y;
+                    finite = finite && isfinite(nw[q].x) && isfinite(nw[q].y);
+                }
+                io.phi_out[c] = phi;
+            } else {
+                T jsum = 0, gsum = 0;
+#pragma unroll
+                for (int q = 0; q < Q; q++) {
+                    io.f_out[q * N + c] = nw[q].x;
+                    finite = finite && isfinite(nw[q].x);
+                    jsum += J[q].y;
+                    if (q > 0) {
+                        io.g_out[q * N + c] = nw[q].y;
+                        gsum += nw[q].y;
+                        finite = finite && isfinite(nw[q].y);
+                    }
+                }
+                const phi_t<T> phi = phi_add(S.phi[TL::i4(x, y)], -(dtv * jsum));
+                io.phi_out[c] = phi;
+                io.g_out[c] = phi_subt(phi, gsum);
+                finite = finite && isfinite(phi_val(phi));
+            }
+            if (!finite) atomicOr(io.status + t.x, ST_NONFINITE);
+        }
+        __syncthreads();
+        if (b + 1 == nblk) break;
+        // ---- carry the top y faces and shift the shared ring rows and their
+        // geometry down by BY (a uniform instance keeps its one row record)
+        for (int k = tid; k < 6 * BX; k += NT) keep[k] = flux[(k / BX) * SL::NFT + L::NFX + (BY - 1) * BX + (k % BX)];
+        for (int r = tid; r < 8; r += NT) {
+            S.gg[L::W4 + r] = S.gg[L::W4 + BY + r];
+            if (!UNI) {
+                S.gf[L::W4 + r] = S.gf[L::W4 + BY + r];
+#pragma unroll
+                for (int k = 0; k < 11; k++) S.ga[k * L::NG + L::W4 + r] = S.ga[k * L::NG + L::W4 + BY + r];
+            }
+        }
+        for (int r = tid; r < 8 * L::W4; r += NT) S.phi[r] = S.phi[BY * L::W4 + r];
+        for (int r = tid; r < 6 * L::W3; r += NT) S.mu[r] = S.mu[BY * L::W3 + r];
+        for (int r = tid; r < 4 * L::W2; r += NT) S.p[r] = S.p[BY * L::W2 + r];
+        // the seven aux planes lie A1 apart from gmx on; then the nine bar-plus pair planes
+        for (int k = tid; k < (7 + Q) * 2 * L::W1; k += NT) {
+            const int pl = k / (2 * L::W1), r = k % (2 * L::W1);
+            if (pl < 7) S.gmx[pl * L::A1 + r] = S.gmx[pl * L::A1 + BY * L::W1 + r];
+            else S.bp[(pl - 7) * L::A1 + r] = S.bp[(pl - 7) * L::A1 + BY * L::W1 + r];
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace dugks

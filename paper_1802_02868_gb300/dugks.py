@@ -353,7 +353,7 @@ def conservation_static(phi_ptr, dx_ptr, dy_ptr, nx, ny, params, out_ptr, stream
                                             ctypes.c_void_p(int(stream)))
 
 
-NUM_TILE_SHAPES = 4
+NUM_TILE_SHAPES = 7
 
 
 def tile_shape_name(k):
