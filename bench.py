@@ -44,13 +44,14 @@ FLOP_PER_CELL_UPDATE = 2127.0
 # lanes x 2 flop x 2.07 GHz, and 152 SMs x 2 DFMA/cycle x 2 flop x 2.07 GHz.
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# DRAM bytes per cell of one k_step launch (the 32x8 tile, uniform periodic
-# path) from an ncu capture of a 2048 x 2048 periodic drop
-# (dram__bytes_read.sum + dram__bytes_write.sum over 4,194,304 cells), valid
-# only for the kernel sources and the tile shape it was taken on.
-TRAFFIC_SOURCES_SHA = "f7e283ceb385259b"
-TRAFFIC_SHAPE = "32x8"
-TRAFFIC_BYTES_PER_CELL_FP32 = (336.531968e6 + 298.570496e6) / 4194304
+# DRAM bytes per cell of one fused-step launch (uniform periodic path), per
+# tile shape, from ncu captures of a 2048 x 2048 periodic drop
+# (dram__bytes_read.sum + dram__bytes_write.sum over 4,194,304 cells); valid
+# only for the kernel sources they were taken on.
+TRAFFIC_SOURCES_SHA = "e825eb5c94e5949b"
+TRAFFIC_BYTES_PER_CELL_FP32 = {
+    "32x8 strip16/288": (348.604160e6 + 302.247936e6) / 4194304,
+}
 
 
 def kernel_sources_sha():
@@ -420,8 +421,8 @@ def main():
     peak_alu = PEAK_FP32_TFLOPS if prec == dugks.FP32 else PEAK_FP64_TFLOPS
     traffic = None
     if kname == "k_step" and prec == dugks.FP32 and kernel_sources_sha() == TRAFFIC_SOURCES_SHA \
-            and tuned[1] == TRAFFIC_SHAPE:
-        traffic = TRAFFIC_BYTES_PER_CELL_FP32 * ncells
+            and tuned[1] in TRAFFIC_BYTES_PER_CELL_FP32:
+        traffic = TRAFFIC_BYTES_PER_CELL_FP32[tuned[1]] * ncells
     roof = {"bound": "alu", "kernel": kname, "achieved": tflops, "peak": peak_alu, "unit": "TFLOP/s",
             "frac": tflops / peak_alu, "peak_source": "unit counts x 2.07 GHz max SM clock (%s)" % (
                 "FP32 FMA lanes" if prec == dugks.FP32 else "FP64 DFMA rate"),
