@@ -17,14 +17,17 @@ def _slices(cases):
     return [slice(off[k], off[k + 1]) for k in range(len(cases))]
 
 
+@pytest.mark.parametrize("shape", range(dugks.NUM_TILE_SHAPES))
 @pytest.mark.parametrize("prec", [dugks.FP64, dugks.FP32])
-def test_step_each_equals_separate_runs(prec):
+def test_step_each_equals_separate_runs(prec, shape):
     """dugks_batch_step_each: every instance ends bit for bit where a run of its
     own count ends; an instance paused beforehand does not move and stays
-    paused."""
+    paused.  Every fused-step shape (tiles and strips) passes a paused
+    instance's state through."""
     cases = I.mobility_sweep(mobilities=(0.01, 0.1, 1.0, 0.3), n=48, radius=12.0)
     counts = [7, 0, 12, 5]
     b = dugks.Sim([c.mesh for c in cases], [c.params for c in cases], prec).init([c.phi0 for c in cases])
+    b.set_tile_shape(shape)
     f0, g0 = b.state()
     b.set_paused([False, False, False, True])
     b.step_each(counts)
