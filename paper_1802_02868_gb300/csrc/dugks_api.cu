@@ -542,8 +542,8 @@ int do_reduce(dugks_sim *s)
 {
     Planes<T> &P = planes<T>(s);
     const dim3 blk(TX, TY);
-    { Timed t(s, K_REDUCE); k_reduce<T><<<(unsigned)s->n_tiles, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, s->d_partials); }
-    { Timed t(s, -1); k_reduce_inst<<<(s->n_inst + 127) / 128, 128, 0, s->stream>>>(s->d_inst, s->n_inst, s->d_partials, s->d_sums); }
+    { Timed t(s, K_REDUCE); k_reduce<T><<<(unsigned)s->n_tiles, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, (const AxisRecT<T> *)s->d_geoT, P, s->d_partials); }
+    { Timed t(s, -1); k_reduce_inst<<<(s->n_inst + 127) / 128, 128, 0, s->stream>>>(s->d_inst, s->n_inst, s->d_partials, s->d_sums, sizeof(T) == sizeof(float) ? 1 : 0); }
     return cuda_status(cudaGetLastError());
 }
 
@@ -874,6 +874,12 @@ int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *para
         for (int j = 0; j < m.ny; j++) dmin = std::min(dmin, m.dy[j]);
         I.dt = p.cfl * dmin / std::sqrt(2.0);          // Eq. (cfl), C_max = sqrt(6 RT) = sqrt(2)
         I.h = 0.5 * I.dt;
+        {
+            double sx = 0.0, sy = 0.0;
+            for (int i = 0; i < m.nx; i++) sx += m.dx[i];
+            for (int j = 0; j < m.ny; j++) sy += m.dy[j];
+            I.vol = sx * sy;
+        }
         I.eta = p.mobility / (p.tau_g / 3.0);           // Eq. (kineticandmobility)
         const double rr = p.rhoA / p.rhoB;
         I.gamma = (rr - 1.0) / (p.phiA - p.phiB * rr);  // Eq. (Gama)
@@ -913,10 +919,11 @@ int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *para
     std::vector<AxisRecT<float>> g32;
     for (const AxisRec &r : geo) {
         AxisRecT<double> a{r.d, r.c1m, r.c10, r.c1p, r.c2m, r.c20, r.c2p, r.e1m, r.e10, r.e1p, r.wL, r.wR, r.invd,
-                           r.km, r.kp, r.lo_wall, r.hi_wall, r.xc};
+                           r.km, r.kp, r.lo_wall, r.hi_wall, r.xc, 0.0};
         AxisRecT<float> b{(float)r.d, (float)r.c1m, (float)r.c10, (float)r.c1p, (float)r.c2m, (float)r.c20,
                           (float)r.c2p, (float)r.e1m, (float)r.e10, (float)r.e1p, (float)r.wL, (float)r.wR,
-                          (float)r.invd, r.km, r.kp, r.lo_wall, r.hi_wall, (float)r.xc};
+                          (float)r.invd, r.km, r.kp, r.lo_wall, r.hi_wall, (float)r.xc,
+                          (float)(r.d - (double)(float)r.d)};
         g64.push_back(a);
         g32.push_back(b);
     }

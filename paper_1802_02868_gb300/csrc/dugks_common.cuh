@@ -105,6 +105,7 @@ struct AxisRecT {
     T d, c1m, c10, c1p, c2m, c20, c2p, e1m, e10, e1p, wL, wR, invd;
     int km, kp, lo_wall, hi_wall;
     T xc;
+    T d_lo;   // d - (T)d of the FP64 width: d + d_lo is the width to about 48 bits in FP32
 };
 
 // A pair (f, g) of values of the two distribution kinds.  In FP32 the pair
@@ -150,6 +151,7 @@ struct InstDev {
     // derived: dt (Eq. cfl), h = dt/2, eta (Eq. kineticandmobility), gamma (Eq. Gama),
     // drho = d rho / d phi (Eq. oderrho)
     double dt, h, eta, gamma, drho;
+    double vol;        // total volume (sum dx)(sum dy)
     // phiA, phiB and (phiA + phiB)/2 as constants of the phi storage
     PhiC cA, cB, cM;
     ParT<double> pd;

@@ -597,28 +597,76 @@ __global__ void __launch_bounds__(TX *TY) k_phi(const InstDev *__restrict__ inst
 // k_reduce: per-tile FP64 partial sums of |V| phi and |V| rho; a second pass
 // (k_reduce_inst) adds the partials of each instance in tile order.
 // ---------------------------------------------------------------------------
+// Double-float arithmetic for the FP32 sums: a value is an unevaluated pair
+// hi + lo of floats.  ff_sum is Knuth's TwoSum, ff_mul Dekker's product with
+// the FMA giving the exact error of hi * hi; both keep about 48 bits, the
+// precision of the stored order parameter.  The _rn intrinsics keep the
+// compiler from contracting the steps whose rounding the algorithms rely on.
+__device__ __forceinline__ void ff_sum(float ah, float al, float bh, float bl, float &sh, float &sl)
+{
+    const float s = __fadd_rn(ah, bh);
+    const float v = __fsub_rn(s, ah);
+    const float e = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, v)), __fsub_rn(bh, v));
+    const float t = __fadd_rn(__fadd_rn(e, al), bl);
+    sh = __fadd_rn(s, t);
+    sl = __fsub_rn(t, __fsub_rn(sh, s));
+}
+__device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, float &ph, float &pl)
+{
+    const float p = __fmul_rn(ah, bh);
+    const float e = __fadd_rn(fmaf(ah, bh, -p), fmaf(ah, bl, __fmul_rn(al, bh)));
+    ph = __fadd_rn(p, e);
+    pl = __fsub_rn(e, __fsub_rn(ph, p));
+}
+
+// k_reduce: per-tile partial sums of |V| phi and |V| rho; a second pass
+// (k_reduce_inst) adds the partials of each instance in tile order.  FP64
+// sims sum in FP64.  FP32 sims sum dx phi along each tile row (a warp) in
+// double-float, multiply by dy and add the rows in FP64; their |V| rho sum is
+// formed per instance from sum |V| phi, because rho is linear in phi (Eq.
+// oderrho): sum |V| rho = rhoB V + (drho)(sum |V| phi - phiB V).
 template <typename T>
 __global__ void __launch_bounds__(TX *TY) k_reduce(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles,
-                                                   const AxisRec *__restrict__ geo, Planes<T> P, double2 *partials)
+                                                   const AxisRec *__restrict__ geo, const AxisRecT<T> *__restrict__ geoT,
+                                                   Planes<T> P, double2 *partials)
 {
     __shared__ double2 red[TX * TY / 32];
     const int4 t = tiles[blockIdx.x];
     const InstDev &I = insts[t.x];
-    const ParT<T> &Pr = par<T>(I);
     const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
-    double a = 0.0, b = 0.0;
-    if (i < I.nx && j < I.ny) {
-        const long long c = cell_of(I, i, j);
-        const double phi = phi_to_double(P.phi[c]);
-        double vol = geo[I.gx_off + i].d * geo[I.gy_off + j].d;
-        a = vol * phi;
-        b = vol * (I.rhoB + I.drho * (phi - I.phiB));
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
-    }
     const int lane = (threadIdx.y * TX + threadIdx.x) & 31, warp = (threadIdx.y * TX + threadIdx.x) >> 5;
+    double a = 0.0, b = 0.0;
+    if constexpr (sizeof(T) == sizeof(float)) {
+        static_assert(TX == 32, "one tile row per warp");
+        float sh = 0.f, sl = 0.f;
+        if (i < I.nx && j < I.ny) {
+            const float2 p = P.phi[cell_of(I, i, j)];
+            const AxisRecT<float> &ax = geoT[I.gx_off + i];
+            ff_mul(ax.d, ax.d_lo, p.x, p.y, sh, sl);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            const float oh = __shfl_down_sync(0xffffffffu, sh, o), ol = __shfl_down_sync(0xffffffffu, sl, o);
+            ff_sum(sh, sl, oh, ol, sh, sl);
+        }
+        if (lane == 0 && j < I.ny) {
+            const AxisRecT<float> &ay = geoT[I.gy_off + j];
+            float rh, rl;
+            ff_mul(sh, sl, ay.d, ay.d_lo, rh, rl);
+            a = (double)rh + (double)rl;
+        }
+    } else {
+        if (i < I.nx && j < I.ny) {
+            const long long c = cell_of(I, i, j);
+            const double phi = phi_to_double(P.phi[c]);
+            double vol = geo[I.gx_off + i].d * geo[I.gy_off + j].d;
+            a = vol * phi;
+            b = vol * (I.rhoB + I.drho * (phi - I.phiB));
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+    }
     if (lane == 0) red[warp] = make_double2(a, b);
     __syncthreads();
     if (threadIdx.x == 0 && threadIdx.y == 0) {
@@ -628,8 +676,9 @@ __global__ void __launch_bounds__(TX *TY) k_reduce(const InstDev *__restrict__ i
     }
 }
 
+// rho_from_phi: form sum |V| rho from sum |V| phi and the total volume (FP32 sims)
 __global__ void k_reduce_inst(const InstDev *__restrict__ insts, int n_inst, const double2 *__restrict__ partials,
-                              double2 *out)
+                              double2 *out, int rho_from_phi)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n_inst) return;
@@ -639,6 +688,7 @@ __global__ void k_reduce_inst(const InstDev *__restrict__ insts, int n_inst, con
         s.x += partials[I.tile0 + t].x;
         s.y += partials[I.tile0 + t].y;
     }
+    if (rho_from_phi) s.y = I.rhoB * I.vol + I.drho * (s.x - I.phiB * I.vol);
     out[k] = s;
 }
 

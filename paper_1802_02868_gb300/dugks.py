@@ -215,8 +215,17 @@ class Sim:
         _check("dugks_step", load().dugks_step(self.h, int(n)))
         return self
 
-    def moments(self):
-        out = [np.zeros(self.ncells) for _ in range(5)]
+    def moments(self, out=None):
+        """phi, rho, ux, uy, p of every cell.  ``out``: five flat contiguous
+        float64 arrays of all cells (for instance views of pinned host memory)
+        that receive the fields directly."""
+        if out is None:
+            out = [np.zeros(self.ncells) for _ in range(5)]
+        else:
+            out = list(out)
+            for a in out:
+                if a.dtype != np.float64 or a.size != self.ncells or not a.flags.c_contiguous:
+                    raise ValueError("moments(out=...): five contiguous float64 arrays of %d cells" % self.ncells)
         _check("dugks_moments", load().dugks_moments(self.h, *[_dp(a) for a in out]))
         return dict(zip(("phi", "rho", "ux", "uy", "p"), [self._split(a) for a in out]))
 
