@@ -57,6 +57,7 @@ struct dugks_sim {
     bool use_graph = true;        // replay multi-step calls from a captured two-step graph
     bool use_uni = true;          // uniform periodic instances take the specialised fused step
     int shape = 0;                // tile shape of the fused step (index into kShapes)
+    int n_sm = 1;                 // multiprocessors of the device (sizes persistent grids)
     // fused-step tile tables per shape: the tiles of uniform periodic instances
     // first (n_uni_s of them), then the rest
     int4 *d_tiles_s[DUGKS_NUM_TILE_SHAPES] = {};
@@ -542,8 +543,10 @@ int do_reduce(dugks_sim *s)
 {
     Planes<T> &P = planes<T>(s);
     const dim3 blk(TX, TY);
-    { Timed t(s, K_REDUCE); k_reduce<T><<<(unsigned)s->n_tiles, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, (const AxisRecT<T> *)s->d_geoT, P, s->d_partials); }
-    { Timed t(s, -1); k_reduce_inst<<<(s->n_inst + 127) / 128, 128, 0, s->stream>>>(s->d_inst, s->n_inst, s->d_partials, s->d_sums, sizeof(T) == sizeof(float) ? 1 : 0); }
+    // FP32: one warp per tile over a grid of 8 blocks per SM; FP64: a block per tile
+    const unsigned g = sizeof(T) == sizeof(float) ? (unsigned)std::min(s->n_tiles, s->n_sm * 8) : (unsigned)s->n_tiles;
+    { Timed t(s, K_REDUCE); k_reduce<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->n_tiles, s->d_geo, (const AxisRecT<T> *)s->d_geoT, P, s->d_partials); }
+    { Timed t(s, -1); k_reduce_inst<<<(s->n_inst + 3) / 4, 128, 0, s->stream>>>(s->d_inst, s->n_inst, s->d_partials, s->d_sums, sizeof(T) == sizeof(float) ? 1 : 0); }
     return cuda_status(cudaGetLastError());
 }
 
@@ -840,6 +843,12 @@ int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *para
         s->use_uni = !(u && u[0] == '1');
     }
     s->stream = (cudaStream_t)cuda_stream;
+    {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+            s->n_sm = nsm;
+    }
     std::vector<AxisRec> geo;
     std::vector<int4> tiles;
     long long cell = 0, dense = 0;

@@ -33,16 +33,16 @@ struct DiagOut {
 
 __device__ __forceinline__ double diag_nan() { return __longlong_as_double(0x7ff8000000000000LL); }
 
-// Arithmetic in the sim's precision T: FP32 sims sum each warp in FP32 (the
-// FP64 pipe of GB300 runs at 1/64 of the FP32 rate) and add the warps in FP64;
-// the crossing heights are placed and compared in FP64.
+// Arithmetic in the sim's precision T: FP32 sims sum each tile in FP32 (the
+// FP64 pipe of GB300 runs at 1/64 of the FP32 rate) and the tiles of an
+// instance in FP64; the crossing heights are placed and compared in FP64.
 template <typename T>
 __global__ void __launch_bounds__(TX *TY) k_diag(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles,
                                                  const AxisRecT<T> *__restrict__ geoT, const AxisRec *__restrict__ geo,
                                                  Planes<T> P, DiagPart *parts, double *p_dense,
                                                  const long long *__restrict__ dense0)
 {
-    __shared__ double red[TX * TY / 32][DIAG_SUMS];
+    __shared__ T red[TX * TY / 32][DIAG_SUMS];
     __shared__ unsigned long long s_front, s_tip;   // bit patterns of positive doubles order as integers
     __shared__ int s_ncross;
     const int4 t = tiles[blockIdx.x];
@@ -99,7 +99,9 @@ __global__ void __launch_bounds__(TX *TY) k_diag(const InstDev *__restrict__ ins
             }
         }
     }
-    // fixed-order reduction: warp shuffles in T, then the warps in order in FP64
+    // fixed-order reduction in T: warp shuffles, then the warps in order, and
+    // one conversion per tile (a warp-wide FP64 instruction occupies GB300's
+    // FP64 pipe for 16 cycles even with one lane active)
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
@@ -107,14 +109,16 @@ __global__ void __launch_bounds__(TX *TY) k_diag(const InstDev *__restrict__ ins
     }
     if (lane == 0) {
 #pragma unroll
-        for (int k = 0; k < DIAG_SUMS; k++) red[warp][k] = (double)v[k];
+        for (int k = 0; k < DIAG_SUMS; k++) red[warp][k] = v[k];
     }
     __syncthreads();
     if (tid == 0) {
         DiagPart out;
-        for (int k = 0; k < DIAG_SUMS; k++) out.s[k] = red[0][k];
-        for (int w = 1; w < TX * TY / 32; w++)
-            for (int k = 0; k < DIAG_SUMS; k++) out.s[k] += red[w][k];
+        for (int k = 0; k < DIAG_SUMS; k++) {
+            T a = red[0][k];
+            for (int w = 1; w < TX * TY / 32; w++) a += red[w][k];
+            out.s[k] = (double)a;
+        }
         out.front = s_ncross ? __longlong_as_double((long long)s_front) : -INFINITY;
         out.tip = s_ncross ? __longlong_as_double((long long)s_tip) : INFINITY;
         parts[blockIdx.x] = out;

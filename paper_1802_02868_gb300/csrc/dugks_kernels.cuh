@@ -621,40 +621,58 @@ __device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, f
 
 // k_reduce: per-tile partial sums of |V| phi and |V| rho; a second pass
 // (k_reduce_inst) adds the partials of each instance in tile order.  FP64
-// sims sum in FP64.  FP32 sims sum dx phi along each tile row (a warp) in
-// double-float, multiply by dy and add the rows in FP64; their |V| rho sum is
-// formed per instance from sum |V| phi, because rho is linear in phi (Eq.
-// oderrho): sum |V| rho = rhoB V + (drho)(sum |V| phi - phiB V).
+// sims: one thread block per tile, sums in FP64.  FP32 sims: one warp per
+// tile over a grid of a few blocks per SM (a block per tile spends most of
+// its time starting and retiring); each lane adds dx dy phi of its column in
+// double-float, the lanes are added in a fixed tree, and the sum is
+// converted once per tile (a warp-wide FP64 instruction occupies GB300's FP64
+// pipe for 16 cycles even with one lane active).
+// Their |V| rho sum is formed per instance from sum |V| phi, because rho is
+// linear in phi (Eq. oderrho): sum |V| rho = rhoB V + (drho)(sum |V| phi - phiB V).
 template <typename T>
 __global__ void __launch_bounds__(TX *TY) k_reduce(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles,
-                                                   const AxisRec *__restrict__ geo, const AxisRecT<T> *__restrict__ geoT,
-                                                   Planes<T> P, double2 *partials)
+                                                   int n_tiles, const AxisRec *__restrict__ geo,
+                                                   const AxisRecT<T> *__restrict__ geoT, Planes<T> P, double2 *partials)
 {
-    __shared__ double2 red[TX * TY / 32];
-    const int4 t = tiles[blockIdx.x];
-    const InstDev &I = insts[t.x];
-    const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
     const int lane = (threadIdx.y * TX + threadIdx.x) & 31, warp = (threadIdx.y * TX + threadIdx.x) >> 5;
-    double a = 0.0, b = 0.0;
     if constexpr (sizeof(T) == sizeof(float)) {
-        static_assert(TX == 32, "one tile row per warp");
-        float sh = 0.f, sl = 0.f;
-        if (i < I.nx && j < I.ny) {
-            const float2 p = P.phi[cell_of(I, i, j)];
-            const AxisRecT<float> &ax = geoT[I.gx_off + i];
-            ff_mul(ax.d, ax.d_lo, p.x, p.y, sh, sl);
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const float oh = __shfl_down_sync(0xffffffffu, sh, o), ol = __shfl_down_sync(0xffffffffu, sl, o);
-            ff_sum(sh, sl, oh, ol, sh, sl);
-        }
-        if (lane == 0 && j < I.ny) {
-            const AxisRecT<float> &ay = geoT[I.gy_off + j];
-            float rh, rl;
-            ff_mul(sh, sl, ay.d, ay.d_lo, rh, rl);
-            a = (double)rh + (double)rl;
+        static_assert(TX == 32, "one tile column per lane");
+        const int nw = gridDim.x * (TX * TY / 32);
+        for (int tt = blockIdx.x * (TX * TY / 32) + warp; tt < n_tiles; tt += nw) {
+            const int4 t = tiles[tt];
+            const InstDev &I = insts[t.x];
+            const int i = t.y + lane;
+            // each lane adds dx dy phi of its column over the tile's rows, then
+            // the lanes are added in a fixed tree
+            float ah = 0.f, al = 0.f;
+            if (i < I.nx) {
+                const AxisRecT<float> &ax = geoT[I.gx_off + i];
+                const float dxh = ax.d, dxl = ax.d_lo;
+#pragma unroll
+                for (int r = 0; r < TY; r++) {
+                    const int j = t.z + r;
+                    if (j < I.ny) {
+                        const float2 p = P.phi[cell_of(I, i, j)];
+                        const AxisRecT<float> &ay = geoT[I.gy_off + j];
+                        float vh, vl, ch, cl;
+                        ff_mul(dxh, dxl, ay.d, ay.d_lo, vh, vl);
+                        ff_mul(vh, vl, p.x, p.y, ch, cl);
+                        ff_sum(ah, al, ch, cl, ah, al);
+                    }
+                }
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const float oh = __shfl_down_sync(0xffffffffu, ah, o), ol = __shfl_down_sync(0xffffffffu, al, o);
+                ff_sum(ah, al, oh, ol, ah, al);
+            }
+            if (lane == 0) partials[tt] = make_double2((double)ah + (double)al, 0.0);
         }
     } else {
+        __shared__ double2 red[TX * TY / 32];
+        const int4 t = tiles[blockIdx.x];
+        const InstDev &I = insts[t.x];
+        const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
+        double a = 0.0, b = 0.0;
         if (i < I.nx && j < I.ny) {
             const long long c = cell_of(I, i, j);
             const double phi = phi_to_double(P.phi[c]);
@@ -666,28 +684,35 @@ __global__ void __launch_bounds__(TX *TY) k_reduce(const InstDev *__restrict__ i
             a += __shfl_down_sync(0xffffffffu, a, o);
             b += __shfl_down_sync(0xffffffffu, b, o);
         }
-    }
-    if (lane == 0) red[warp] = make_double2(a, b);
-    __syncthreads();
-    if (threadIdx.x == 0 && threadIdx.y == 0) {
-        double2 s = red[0];
-        for (int w = 1; w < TX * TY / 32; w++) { s.x += red[w].x; s.y += red[w].y; }
-        partials[blockIdx.x] = s;
+        if (lane == 0) red[warp] = make_double2(a, b);
+        __syncthreads();
+        if (threadIdx.x == 0 && threadIdx.y == 0) {
+            double2 s = red[0];
+            for (int w = 1; w < TX * TY / 32; w++) { s.x += red[w].x; s.y += red[w].y; }
+            partials[blockIdx.x] = s;
+        }
     }
 }
 
-// rho_from_phi: form sum |V| rho from sum |V| phi and the total volume (FP32 sims)
+// One warp per instance: lane l adds tiles l, l + 32, ... in order, then the
+// lanes are added in a fixed tree.  rho_from_phi: form sum |V| rho from sum
+// |V| phi and the total volume (FP32 sims).
 __global__ void k_reduce_inst(const InstDev *__restrict__ insts, int n_inst, const double2 *__restrict__ partials,
                               double2 *out, int rho_from_phi)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (k >= n_inst) return;
     const InstDev &I = insts[k];
     double2 s = make_double2(0.0, 0.0);
-    for (int t = 0; t < I.ntiles; t++) {
+    for (int t = lane; t < I.ntiles; t += 32) {
         s.x += partials[I.tile0 + t].x;
         s.y += partials[I.tile0 + t].y;
     }
+    for (int o = 16; o > 0; o >>= 1) {
+        s.x += __shfl_down_sync(0xffffffffu, s.x, o);
+        s.y += __shfl_down_sync(0xffffffffu, s.y, o);
+    }
+    if (lane != 0) return;
     if (rho_from_phi) s.y = I.rhoB * I.vol + I.drho * (s.x - I.phiB * I.vol);
     out[k] = s;
 }
