@@ -74,6 +74,22 @@ typedef struct {
 
 typedef struct dugks_sim dugks_sim; /* opaque, library-owned */
 
+/* Device memory from the caller: a caller that manages device memory itself
+   (for instance through PyTorch's caching allocator) supplies the library's
+   device memory.  The paper has no counterpart.  alloc(bytes, stream, ctx) returns device memory of at
+   least `bytes` bytes, aligned to 256 bytes, usable on `stream` (the stream
+   the sim was created with), or NULL; release(ptr, stream, ctx) returns it.
+   The pair applies to the sims created after the call, for their whole life:
+   their planes and tables, and the temporary buffers of dugks_autotune,
+   dugks_adjoint and the diagnostics.  NULL, NULL restores cudaMalloc and
+   cudaFree.  Passing only one of the two is DUGKS_ERR_ARG.  An alloc that
+   returns NULL makes the call that needed the memory fail with
+   DUGKS_ERR_OOM.  The setting is process-wide and not synchronised: set it
+   before creating sims from several threads. */
+typedef void *(*dugks_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*dugks_free_fn)(void *ptr, void *stream, void *ctx);
+int dugks_set_allocator(dugks_alloc_fn alloc, dugks_free_fn release, void *ctx);
+
 /* Create one simulation on the current CUDA device; stream may be NULL (the
    legacy default stream).  Validates the mesh and parameters (ERR_ARG),
    allocates device state (ERR_OOM on failure) and uploads the geometry. */

@@ -58,6 +58,10 @@ struct dugks_sim {
     bool use_uni = true;          // uniform periodic instances take the specialised fused step
     int shape = 0;                // tile shape of the fused step (index into kShapes)
     int n_sm = 1;                 // multiprocessors of the device (sizes persistent grids)
+    // device memory source, fixed at creation (dugks_set_allocator)
+    dugks_alloc_fn alloc_fn = nullptr;
+    dugks_free_fn free_fn = nullptr;
+    void *alloc_ctx = nullptr;
     // fused-step tile tables per shape: the tiles of uniform periodic instances
     // first (n_uni_s of them), then the rest
     int4 *d_tiles_s[DUGKS_NUM_TILE_SHAPES] = {};
@@ -107,6 +111,26 @@ int cuda_status(cudaError_t e)
     if (e == cudaSuccess) return DUGKS_OK;
     if (e == cudaErrorMemoryAllocation) return DUGKS_ERR_OOM;
     return DUGKS_ERR_CUDA;
+}
+
+// the allocator that dugks_create hands to the next sims
+dugks_alloc_fn g_alloc_fn = nullptr;
+dugks_free_fn g_free_fn = nullptr;
+void *g_alloc_ctx = nullptr;
+
+// device memory of a sim, from the caller's allocator when one was set
+cudaError_t dmalloc(dugks_sim *s, void **p, size_t bytes)
+{
+    if (!s->alloc_fn) return cudaMalloc(p, bytes);
+    *p = s->alloc_fn(bytes, (void *)s->stream, s->alloc_ctx);
+    return (*p || bytes == 0) ? cudaSuccess : cudaErrorMemoryAllocation;
+}
+
+void dfree(dugks_sim *s, void *p)
+{
+    if (!p) return;
+    if (s->free_fn) s->free_fn(p, (void *)s->stream, s->alloc_ctx);
+    else cudaFree(p);
 }
 
 bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
@@ -298,10 +322,10 @@ int ensure_tiles(dugks_sim *s, int k)
         }
         if (pass == 0) s->n_uni_s[k] = (int)tiles.size();
     }
-    cudaError_t e = cudaMalloc(&s->d_tiles_s[k], sizeof(int4) * tiles.size());
+    cudaError_t e = dmalloc(s, (void **)&s->d_tiles_s[k], sizeof(int4) * tiles.size());
     if (e == cudaSuccess) e = cudaMemcpy(s->d_tiles_s[k], tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        cudaFree(s->d_tiles_s[k]);
+        dfree(s, s->d_tiles_s[k]);
         s->d_tiles_s[k] = nullptr;
         return cuda_status(e);
     }
@@ -556,10 +580,10 @@ template <typename T>
 int do_diag(dugks_sim *s, double *p_dense)
 {
     if (!s->d_diag_parts) {
-        cudaError_t e = cudaMalloc(&s->d_diag_parts, sizeof(DiagPart) * s->n_tiles);
-        if (e == cudaSuccess) e = cudaMalloc(&s->d_diag_out, sizeof(DiagOut) * s->n_inst);
+        cudaError_t e = dmalloc(s, (void **)&s->d_diag_parts, sizeof(DiagPart) * s->n_tiles);
+        if (e == cudaSuccess) e = dmalloc(s, (void **)&s->d_diag_out, sizeof(DiagOut) * s->n_inst);
         if (e != cudaSuccess) {
-            cudaFree(s->d_diag_parts);
+            dfree(s, s->d_diag_parts);
             s->d_diag_parts = nullptr;
             return cuda_status(e);
         }
@@ -600,23 +624,23 @@ constexpr int kNumScalarPlanes = 12;
 void free_sim(dugks_sim *s)
 {
     if (!s) return;
-    cudaFree(s->d_inst);
-    cudaFree(s->d_tiles);
-    for (int k = 0; k < DUGKS_NUM_TILE_SHAPES; k++) cudaFree(s->d_tiles_s[k]);
-    cudaFree(s->d_geo);
-    cudaFree(s->d_geoT);
-    cudaFree(s->d_dense0);
-    cudaFree(s->d_planes);
-    cudaFree(s->d_phi);
-    cudaFree(s->d_alt_alloc);
-    cudaFree(s->d_phi_alt_alloc);
-    cudaFree(s->d_status);
-    cudaFree(s->d_partials);
-    cudaFree(s->d_sums);
-    cudaFree(s->d_stage);
-    cudaFree(s->d_init_in);
-    cudaFree(s->d_diag_parts);
-    cudaFree(s->d_diag_out);
+    dfree(s, s->d_inst);
+    dfree(s, s->d_tiles);
+    for (int k = 0; k < DUGKS_NUM_TILE_SHAPES; k++) dfree(s, s->d_tiles_s[k]);
+    dfree(s, s->d_geo);
+    dfree(s, s->d_geoT);
+    dfree(s, s->d_dense0);
+    dfree(s, s->d_planes);
+    dfree(s, s->d_phi);
+    dfree(s, s->d_alt_alloc);
+    dfree(s, s->d_phi_alt_alloc);
+    dfree(s, s->d_status);
+    dfree(s, s->d_partials);
+    dfree(s, s->d_sums);
+    dfree(s, s->d_stage);
+    dfree(s, s->d_init_in);
+    dfree(s, s->d_diag_parts);
+    dfree(s, s->d_diag_out);
     if (s->graph2) cudaGraphExecDestroy(s->graph2);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     for (auto &e : s->ev_used) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
@@ -676,7 +700,7 @@ int adjoint_impl(dugks_sim *s, long nsteps, int K, const double *target_h, doubl
     const size_t scal_planes = 13;
     const size_t bytes = w.state_bytes * (size_t)(nck + 1 + K) + sizeof(T) * (size_t)N * (2 * 2 * Q + 2 * Q + scal_planes + 2 * Q)
                        + sizeof(double) * (size_t)(2 * n + n + 2 * D);
-    cudaError_t e = cudaMalloc(&w.mem, bytes);
+    cudaError_t e = dmalloc(s, (void **)&w.mem, bytes);
     if (e != cudaSuccess) return cuda_status(e);
     unsigned char *m = (unsigned char *)w.mem;
     w.ckpt = m; m += w.state_bytes * (size_t)(nck + 1);
@@ -793,7 +817,7 @@ int adjoint_impl(dugks_sim *s, long nsteps, int K, const double *target_h, doubl
     P.fbp = save_fbp;
     P.gbp = save_gbp;
     s->timing = timing;
-    cudaFree(w.mem);
+    dfree(s, w.mem);
     return rc;
 }
 
@@ -843,6 +867,9 @@ int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *para
         s->use_uni = !(u && u[0] == '1');
     }
     s->stream = (cudaStream_t)cuda_stream;
+    s->alloc_fn = g_alloc_fn;
+    s->free_fn = g_free_fn;
+    s->alloc_ctx = g_alloc_ctx;
     {
         int dev = 0, nsm = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
@@ -920,9 +947,9 @@ int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *para
     const size_t plane_elems = (size_t)((s->fused ? 2 : 4) * Q + kNumScalarPlanes) * (size_t)s->N;
     cudaError_t e = cudaSuccess;
     auto chk = [&](cudaError_t r) { if (r != cudaSuccess && e == cudaSuccess) e = r; };
-    chk(cudaMalloc(&s->d_inst, sizeof(InstDev) * n));
-    chk(cudaMalloc(&s->d_tiles, sizeof(int4) * tiles.size()));
-    chk(cudaMalloc(&s->d_geo, sizeof(AxisRec) * geo.size()));
+    chk(dmalloc(s, (void **)&s->d_inst, sizeof(InstDev) * n));
+    chk(dmalloc(s, (void **)&s->d_tiles, sizeof(int4) * tiles.size()));
+    chk(dmalloc(s, (void **)&s->d_geo, sizeof(AxisRec) * geo.size()));
     // typed copy of the geometry for the fused step
     std::vector<AxisRecT<double>> g64;
     std::vector<AxisRecT<float>> g32;
@@ -938,19 +965,19 @@ int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *para
     }
     const bool is64 = s->prec == DUGKS_FP64;
     const size_t geoT_bytes = is64 ? sizeof(AxisRecT<double>) * g64.size() : sizeof(AxisRecT<float>) * g32.size();
-    chk(cudaMalloc(&s->d_geoT, geoT_bytes));
-    chk(cudaMalloc(&s->d_dense0, sizeof(long long) * n));
-    chk(cudaMalloc(&s->d_planes, esz * plane_elems));
-    chk(cudaMalloc(&s->d_phi, sizeof(double) * (size_t)s->N));
-    chk(cudaMalloc(&s->d_alt_alloc, esz * 2 * Q * (size_t)s->N));
-    chk(cudaMalloc(&s->d_phi_alt_alloc, sizeof(double) * (size_t)s->N));
+    chk(dmalloc(s, (void **)&s->d_geoT, geoT_bytes));
+    chk(dmalloc(s, (void **)&s->d_dense0, sizeof(long long) * n));
+    chk(dmalloc(s, (void **)&s->d_planes, esz * plane_elems));
+    chk(dmalloc(s, (void **)&s->d_phi, sizeof(double) * (size_t)s->N));
+    chk(dmalloc(s, (void **)&s->d_alt_alloc, esz * 2 * Q * (size_t)s->N));
+    chk(dmalloc(s, (void **)&s->d_phi_alt_alloc, sizeof(double) * (size_t)s->N));
     s->d_alt = s->d_alt_alloc;
     s->d_phi_alt = s->d_phi_alt_alloc;
-    chk(cudaMalloc(&s->d_status, sizeof(int) * n));
-    chk(cudaMalloc(&s->d_partials, sizeof(double2) * tiles.size()));
-    chk(cudaMalloc(&s->d_sums, sizeof(double2) * n));
-    chk(cudaMalloc(&s->d_stage, sizeof(double) * (size_t)std::max<long long>(5, 2 * Q) * (size_t)dense));
-    chk(cudaMalloc(&s->d_init_in, sizeof(double) * 4 * (size_t)dense));
+    chk(dmalloc(s, (void **)&s->d_status, sizeof(int) * n));
+    chk(dmalloc(s, (void **)&s->d_partials, sizeof(double2) * tiles.size()));
+    chk(dmalloc(s, (void **)&s->d_sums, sizeof(double2) * n));
+    chk(dmalloc(s, (void **)&s->d_stage, sizeof(double) * (size_t)std::max<long long>(5, 2 * Q) * (size_t)dense));
+    chk(dmalloc(s, (void **)&s->d_init_in, sizeof(double) * 4 * (size_t)dense));
     if (e != cudaSuccess) {
         int rc = cuda_status(e);
         free_sim(s);
@@ -1298,7 +1325,7 @@ int dugks_autotune(dugks_sim *s, int steps, int *chosen, double *ms_per_step)
     const size_t st_bytes = sizeof(int) * s->n_inst;
     // snapshot of the current state, restored after every trial
     void *snap = nullptr;
-    cudaError_t e = cudaMalloc(&snap, fg_bytes + phi_bytes + st_bytes);
+    cudaError_t e = dmalloc(s, (void **)&snap, fg_bytes + phi_bytes + st_bytes);
     if (e != cudaSuccess) return cuda_status(e);
     auto cur = [&](void **fg, void **phi) {
         if (f64) { *fg = s->P64.f; *phi = s->P64.phi; }
@@ -1341,7 +1368,7 @@ int dugks_autotune(dugks_sim *s, int steps, int *chosen, double *ms_per_step)
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (a) cudaEventDestroy(a);
     if (b) cudaEventDestroy(b);
-    cudaFree(snap);
+    dfree(s, snap);
     s->timing = timing;
     s->launches = launches;
     if (rc == DUGKS_OK && e != cudaSuccess) rc = cuda_status(e);
@@ -1351,6 +1378,15 @@ int dugks_autotune(dugks_sim *s, int steps, int *chosen, double *ms_per_step)
         if (ms_per_step) *ms_per_step = best_ms / steps;
     }
     return rc;
+}
+
+int dugks_set_allocator(dugks_alloc_fn alloc, dugks_free_fn release, void *ctx)
+{
+    if ((alloc == nullptr) != (release == nullptr)) return DUGKS_ERR_ARG;
+    g_alloc_fn = alloc;
+    g_free_fn = release;
+    g_alloc_ctx = alloc ? ctx : nullptr;
+    return DUGKS_OK;
 }
 
 int dugks_uniform_instances(const dugks_sim *s, int *n)

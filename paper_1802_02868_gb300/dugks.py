@@ -11,8 +11,10 @@ stream is the caller's (``torch.cuda.current_stream().cuda_stream`` or 0).
 """
 from __future__ import annotations
 
+import atexit
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -50,6 +52,63 @@ class Params_t(ctypes.Structure):
                [("precision", ctypes.c_int)]
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_allocator = None          # the callbacks in use (kept alive while sims may call them)
+_allocator_sims = []       # weak references to sims that use them, closed at exit
+
+
+def set_allocator(alloc=None, release=None):
+    """Device memory for the sims created from now on: ``alloc(nbytes, stream)``
+    returns a device pointer (int, 0 on failure) and ``release(ptr, stream)``
+    frees it (dugks_set_allocator); with no arguments cudaMalloc/cudaFree
+    come back."""
+    global _allocator
+    if alloc is None:
+        _check("dugks_set_allocator", load().dugks_set_allocator(ALLOC_FN(), FREE_FN(), None))
+        _allocator = None
+        return
+
+    def _a(n, stream, ctx):
+        try:
+            return int(alloc(int(n), stream or 0)) or None
+        except Exception:
+            return None
+
+    def _f(p, stream, ctx):
+        try:
+            release(int(p), stream or 0)
+        except Exception:
+            pass
+
+    cb = (ALLOC_FN(_a), FREE_FN(_f))
+    _check("dugks_set_allocator", load().dugks_set_allocator(cb[0], cb[1], None))
+    _allocator = cb
+
+
+def use_torch_allocator():
+    """Take the device memory of new sims from PyTorch's caching allocator."""
+    import torch
+
+    def alloc(n, stream):
+        return torch.cuda.caching_allocator_alloc(n, torch.cuda.current_device(), stream)
+
+    def release(p, stream):
+        torch.cuda.caching_allocator_delete(p)
+
+    set_allocator(alloc, release)
+
+
+def _close_allocator_sims():
+    for ref in _allocator_sims:
+        sim = ref()
+        if sim is not None:
+            sim.close()
+
+
+atexit.register(_close_allocator_sims)
+
+
 class Diag_t(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in DIAG_FIELDS]
 
@@ -61,7 +120,7 @@ EXPORTS = ("dugks_create", "dugks_batch_create", "dugks_destroy", "dugks_init", 
            "dugks_kernel_bytes_per_cell", "dugks_status_str", "dugks_conservation_static",
            "dugks_autotune", "dugks_set_tile_shape", "dugks_tile_shape", "dugks_tile_shape_name",
            "dugks_adjoint", "dugks_uniform_instances", "dugks_diagnostics", "dugks_laplace_pressure",
-           "dugks_batch_set_paused", "dugks_batch_step_each")
+           "dugks_batch_set_paused", "dugks_batch_step_each", "dugks_set_allocator")
 STATIC_MAX_CELLS = 16777216
 
 
@@ -110,6 +169,7 @@ def load(build_if_missing: bool = True):
     L.dugks_laplace_pressure.argtypes = [vp, dp]
     L.dugks_batch_set_paused.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.dugks_batch_step_each.argtypes = [vp, ctypes.POINTER(ctypes.c_long)]
+    L.dugks_set_allocator.argtypes = [ALLOC_FN, FREE_FN, vp]
     L.dugks_tile_shape_name.argtypes = [ip]
     L.dugks_tile_shape_name.restype = ctypes.c_char_p
     L.dugks_status_str.argtypes = [ip]
@@ -168,6 +228,11 @@ class Sim:
         rc = L.dugks_batch_create(n, M, Pr, ctypes.c_void_p(int(stream)), ctypes.byref(h))
         _check("dugks_batch_create", rc)
         self.h = h
+        # a sim created with caller callbacks keeps them alive, and is closed at
+        # exit while they still can run
+        self._allocator = _allocator
+        if _allocator is not None:
+            _allocator_sims.append(weakref.ref(self))
         self.precision = precision
         self.sizes = [m.nx * m.ny for m in self.meshes]
         self.ncells = int(sum(self.sizes))

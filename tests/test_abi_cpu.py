@@ -67,3 +67,15 @@ def test_invalid_arguments_rejected_before_device_work(bad):
 def test_status_strings():
     assert dugks.status_str(0) == "ok"
     assert dugks.status_str(-3) == "non-finite state"
+
+
+def test_set_allocator_needs_both_callbacks():
+    """dugks_set_allocator takes an alloc/release pair or neither (host-only
+    check; nothing is allocated)."""
+    L = dugks.load()
+    alloc = dugks.ALLOC_FN(lambda n, st, ctx: None)
+    assert L.dugks_set_allocator(alloc, dugks.FREE_FN(), None) == -1
+    assert L.dugks_set_allocator(dugks.ALLOC_FN(), dugks.FREE_FN(), None) == 0
+    dugks.set_allocator(lambda n, st: 0, lambda p, st: None)
+    dugks.set_allocator()
+    assert dugks._allocator is None

@@ -270,3 +270,36 @@ def test_fp32_conservation_sums_match_fp64_sums_of_the_state():
         rho = p.rhoB + (p.rhoA - p.rhoB) * (phi - p.phiB) / (p.phiA - p.phiB)   # Eq. oderrho in FP64
         assert sp[k] == pytest.approx(float(np.sum(vol * phi)), rel=1e-12)
         assert sr[k] == pytest.approx(float(np.sum(vol * rho)), rel=1e-12)
+
+
+def test_caller_allocator_supplies_device_memory():
+    """dugks_set_allocator: sims created after it take their device memory from
+    the caller (here PyTorch's caching allocator) and step exactly like
+    cudaMalloc-backed sims; an allocator that fails makes creation fail with
+    DUGKS_ERR_OOM; unsetting restores cudaMalloc."""
+    import torch
+    c = CASES[3][1]
+    ref = dugks.Sim(c.mesh, c.params, dugks.FP32).init(c.phi0)
+    ref.step(9)
+    torch.cuda.synchronize()
+    before = torch.cuda.memory_allocated()
+    dugks.use_torch_allocator()
+    try:
+        s = dugks.Sim(c.mesh, c.params, dugks.FP32).init(c.phi0)
+        held = torch.cuda.memory_allocated() - before
+        assert held >= 2 * 2 * 9 * 4 * c.mesh.ncells      # both state buffers at least
+        s.set_tile_shape(dugks.NUM_TILE_SHAPES - 1)
+        s.step(9)
+        for a, b in zip(s.state(), ref.state()):
+            assert np.array_equal(a, b)
+        s.close()
+        assert torch.cuda.memory_allocated() == before
+        dugks.set_allocator(lambda n, st: 0, lambda p, st: None)
+        with pytest.raises(dugks.DugksError) as e:
+            dugks.Sim(c.mesh, c.params, dugks.FP32)
+        assert e.value.rc == -4
+    finally:
+        dugks.set_allocator()
+    s = dugks.Sim(c.mesh, c.params, dugks.FP32)
+    assert torch.cuda.memory_allocated() == before
+    s.close()
