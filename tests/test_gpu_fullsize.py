@@ -133,3 +133,28 @@ def test_checkpoint_resume_is_exact():
             # FP32 carries phi as a float pair; the checkpoint stores the tilde
             # state in FP64, from which phi = sum g is rebuilt on load
             assert normwise(fb, fa) < 1e-5 and normwise(gb, ga) < 1e-6
+
+
+def test_maximum_size_mesh_matches_narrow_oracle_by_translation_invariance():
+    """A 4,194,304 x 64 periodic mesh (2.7e8 cells, plane offsets past 2^31,
+    about 100 GB of device memory) with a field that depends on y only: every
+    column must equal the oracle's run on a 4 x 64 mesh (translation
+    invariance in x), checked on the first, middle and last columns."""
+    nx, ny, steps = 1 << 22, 64, 2
+    beta, kappa = I.params_from_sigma_width(1e-3, 4.0)
+    p = I.Params(rhoA=2.0, rhoB=1.0, beta=beta, kappa=kappa, gy=-1e-5, rho_ref=1.5)
+    narrow = I.Mesh(np.ones(4), np.ones(ny))
+    col = I.layered_field(narrow, 0.4 * ny, 4.0)[:, 0] + 0.05 * np.sin(2 * np.pi * np.arange(ny) / ny)
+    o = oracle.Oracle(narrow, p).init(np.repeat(col[:, None], 4, axis=1))
+    o.step(steps)
+    mo = o.moments()
+    wide = I.Mesh(np.ones(nx), np.ones(ny))
+    s = dugks.Sim(wide, p, dugks.FP32).init(np.repeat(col[:, None], nx, axis=1))
+    s.step(steps)
+    ms = s.moments()
+    for name, tol in (("phi", 1e-6), ("rho", 1e-6), ("uy", 1e-4), ("p", 1e-4)):
+        ref = mo[name][:, 0]
+        scale = max(np.max(np.abs(ref)), 1e-12)
+        for c in (0, 1, nx // 2, nx - 33, nx - 1):
+            assert np.max(np.abs(ms[name][:, c] - ref)) <= tol * scale, (name, c)
+    s.close()
