@@ -48,7 +48,7 @@ PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # tile shape, from ncu captures of a 2048 x 2048 periodic drop
 # (dram__bytes_read.sum + dram__bytes_write.sum over 4,194,304 cells); valid
 # only for the kernel sources they were taken on.
-TRAFFIC_SOURCES_SHA = "e825eb5c94e5949b"
+TRAFFIC_SOURCES_SHA = "c1c0e66b9e8556a8"
 TRAFFIC_BYTES_PER_CELL_FP32 = {
     "32x8 strip16/288": (348.604160e6 + 302.247936e6) / 4194304,
 }

@@ -378,8 +378,53 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
         __syncthreads();
         if (b + 1 == nblk) break;
         // ---- carry the top y faces and shift the shared ring rows and their
-        // geometry down by BY (a uniform instance keeps its one row record)
-        for (int k = tid; k < 6 * BX; k += NT) keep[k] = flux[(k / BX) * SL::NFT + L::NFX + (BY - 1) * BX + (k % BX)];
+        // geometry down by BY (a uniform instance keeps its one row record).
+        // The rows of a ring are contiguous and 16-byte aligned, so they move
+        // in 16-byte words: one pass over all the segments.
+        {
+            constexpr int KB = (int)(sizeof(pair_t<T>) * BX / 16);              // carried faces, per direction
+            constexpr int PHB = (int)(sizeof(phi_t<T>) * 8 * L::W4 / 16);
+            constexpr int MUB = (int)(sizeof(T) * 6 * L::W3 / 16);
+            constexpr int PB = (int)(sizeof(T) * 4 * L::W2 / 16);
+            constexpr int AB = (int)(sizeof(T) * 2 * L::W1 / 16);               // one aux plane
+            constexpr int BB = (int)(sizeof(pair_t<T>) * 2 * L::W1 / 16);       // one bar-plus plane
+            static_assert(sizeof(pair_t<T>) * BX % 16 == 0 && sizeof(phi_t<T>) * 8 * L::W4 % 16 == 0 &&
+                              sizeof(T) * 6 * L::W3 % 16 == 0 && sizeof(T) * 4 * L::W2 % 16 == 0 &&
+                              sizeof(T) * 2 * L::W1 % 16 == 0 && sizeof(T) * L::A1 % 16 == 0 &&
+                              sizeof(T) * BY * L::W3 % 16 == 0 && sizeof(T) * BY * L::W2 % 16 == 0 &&
+                              sizeof(T) * BY * L::W1 % 16 == 0 && sizeof(pair_t<T>) * SL::NFT % 16 == 0 &&
+                              sizeof(pair_t<T>) * (L::NFX + (BY - 1) * BX) % 16 == 0,
+                          "16-byte ring rows");
+            constexpr int NKEEP = 6 * KB, NPHI = NKEEP + PHB, NMU = NPHI + MUB, NP = NMU + PB, NAUX = NP + 7 * AB;
+            constexpr int NALL = NAUX + Q * BB;
+            for (int k = tid; k < NALL; k += NT) {
+                float4 *d;
+                const float4 *src;
+                if (k < NKEEP) {
+                    const int m = k / KB, w = k % KB;
+                    d = (float4 *)(keep + m * BX) + w;
+                    src = (const float4 *)(flux + m * SL::NFT + L::NFX + (BY - 1) * BX) + w;
+                } else if (k < NPHI) {
+                    d = (float4 *)S.phi + (k - NKEEP);
+                    src = (const float4 *)(S.phi + BY * L::W4) + (k - NKEEP);
+                } else if (k < NMU) {
+                    d = (float4 *)S.mu + (k - NPHI);
+                    src = (const float4 *)(S.mu + BY * L::W3) + (k - NPHI);
+                } else if (k < NP) {
+                    d = (float4 *)S.p + (k - NMU);
+                    src = (const float4 *)(S.p + BY * L::W2) + (k - NMU);
+                } else if (k < NAUX) {
+                    const int pl = (k - NP) / AB, w = (k - NP) % AB;
+                    d = (float4 *)(S.gmx + pl * L::A1) + w;
+                    src = (const float4 *)(S.gmx + pl * L::A1 + BY * L::W1) + w;
+                } else {
+                    const int q = (k - NAUX) / BB, w = (k - NAUX) % BB;
+                    d = (float4 *)(S.bp + q * L::A1) + w;
+                    src = (const float4 *)(S.bp + q * L::A1 + BY * L::W1) + w;
+                }
+                *d = *src;
+            }
+        }
         for (int r = tid; r < 8; r += NT) {
             S.gg[L::W4 + r] = S.gg[L::W4 + BY + r];
             if (!UNI) {
@@ -387,15 +432,6 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
 #pragma unroll
                 for (int k = 0; k < 11; k++) S.ga[k * L::NG + L::W4 + r] = S.ga[k * L::NG + L::W4 + BY + r];
             }
-        }
-        for (int r = tid; r < 8 * L::W4; r += NT) S.phi[r] = S.phi[BY * L::W4 + r];
-        for (int r = tid; r < 6 * L::W3; r += NT) S.mu[r] = S.mu[BY * L::W3 + r];
-        for (int r = tid; r < 4 * L::W2; r += NT) S.p[r] = S.p[BY * L::W2 + r];
-        // the seven aux planes lie A1 apart from gmx on; then the nine bar-plus pair planes
-        for (int k = tid; k < (7 + Q) * 2 * L::W1; k += NT) {
-            const int pl = k / (2 * L::W1), r = k % (2 * L::W1);
-            if (pl < 7) S.gmx[pl * L::A1 + r] = S.gmx[pl * L::A1 + BY * L::W1 + r];
-            else S.bp[(pl - 7) * L::A1 + r] = S.bp[(pl - 7) * L::A1 + BY * L::W1 + r];
         }
         __syncthreads();
     }
