@@ -50,7 +50,7 @@ PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # only for the kernel sources they were taken on.
 TRAFFIC_SOURCES_SHA = "c1c0e66b9e8556a8"
 TRAFFIC_BYTES_PER_CELL_FP32 = {
-    "32x8 strip16/288": (348.604160e6 + 302.247936e6) / 4194304,
+    "32x8 strip16/288": (348.848128e6 + 301.476352e6) / 4194304,
 }
 
 
