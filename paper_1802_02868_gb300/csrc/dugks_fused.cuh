@@ -239,8 +239,11 @@ __device__ __forceinline__ void tile_face(const InstDev &I, const TL &S, int xa,
             const T k1 = h * T(ca(q, A)) * invd;
             pair_t<T> v = pfma(pr(wL + k1), bL, pmul(pr(wR - k1), bR));
             if (ca(q, 1 - A)) {
-                const pair_t<T> tL = pfma(pr(te1m), B[ia + tm], pfma(pr(te10), bL, pmul(pr(te1p), B[ia + tp])));
-                const pair_t<T> tR = pfma(pr(te1m), B[ib + tm], pfma(pr(te10), bR, pmul(pr(te1p), B[ib + tp])));
+                // the centre weight is exactly 0 on a uniform periodic axis
+                const pair_t<T> tL = UNI ? pfma(pr(te1m), B[ia + tm], pmul(pr(te1p), B[ia + tp]))
+                                         : pfma(pr(te1m), B[ia + tm], pfma(pr(te10), bL, pmul(pr(te1p), B[ia + tp])));
+                const pair_t<T> tR = UNI ? pfma(pr(te1m), B[ib + tm], pmul(pr(te1p), B[ib + tp]))
+                                         : pfma(pr(te1m), B[ib + tm], pfma(pr(te10), bR, pmul(pr(te1p), B[ib + tp])));
                 const T kt = -h * T(ca(q, 1 - A));
                 v = pfma(pr(kt * wL), tL, pfma(pr(kt * wR), tR, v));
             }
