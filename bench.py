@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -118,7 +119,9 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % os.getpid())
+        # raw samples: DUGKS_CLOCKS_DIR if set, else the temporary directory
+        folder = os.environ.get("DUGKS_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(folder, "clocks_bench_%d.csv" % os.getpid())
 
     def start(self):
         try:
