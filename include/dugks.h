@@ -156,8 +156,8 @@ int dugks_load(dugks_sim *sim, const void *buf, size_t bytes);
 
 /* Adjoint (reverse-mode gradient) of L = sum over all cells of
    (phi_T - phi_target)^2, phi_T the order parameter after nsteps steps from
-   the last dugks_init inputs (the spec differentiation form; the
-   forward step is Sec. 2.2's procedure, the gradient is its exact transpose).
+   the last dugks_init inputs (the forward step is Sec. 2.2's procedure, the
+   gradient is its exact transpose).
    The forward run is replayed from the saved init inputs with a checkpoint of
    the state every ckpt_every steps; each segment is recomputed and swept
    backwards.  Outputs (host, each may be NULL): loss[n_instances],
@@ -166,7 +166,7 @@ int dugks_load(dugks_sim *sim, const void *buf, size_t bytes);
    the mobility).  phi_target: host array of all cells.  Allocates its
    checkpoints and work planes for the duration of the call and synchronises;
    the simulation is left at the final forward state.  ERR_ARG if the sim was
-   never initialised. */
+   never initialised or an instance is paused (dugks_batch_set_paused). */
 int dugks_adjoint(dugks_sim *sim, long nsteps, int ckpt_every, const double *phi_target, double *loss,
                   double *dL_dphi0, double *dL_dkappa, double *dL_dlambda);
 
