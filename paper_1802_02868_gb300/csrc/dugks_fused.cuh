@@ -192,13 +192,15 @@ __device__ __forceinline__ void face_tail(const InstDev &I, const T (&fb)[Q], co
     const pair_t<T> ca2 = pr(a1, a2), cb2 = pr(b1, b2), cc2 = pr(c1, c2);
     pair_t<T> o[Q];
 #pragma unroll
-    for (int k = 0; k < 6; k++) {
-        const int q = fset<A>(k);
-        // at a wall only the outgoing originals are formed; incoming ones bounce back
-        if (wall && ca(q, A) * side < 0) continue;
-        T feq, geq, F1, F2;
-        eq_src<T>(s, v, q, feq, geq, F1, F2);
-        o[q] = pfma(ca2, pr(fb[q], gb[q]), pfma(cb2, pr(feq, geq), pmul(cc2, pr(F1, F2))));
+    for (int k = 0; k < 3; k++) {
+        // the six directions as three opposite pairs; at a wall the incoming
+        // originals are formed too but replaced by bounce-back below
+        const int q = k == 0 ? fset<A>(0) : k + 4;   // 1|3 or 2|4, 5|7, 6|8
+        T feq[2], geq[2], F1[2], F2[2];
+        eq_src2<T>(s, v, q, feq, geq, F1, F2);
+        o[q] = pfma(ca2, pr(fb[q], gb[q]), pfma(cb2, pr(feq[0], geq[0]), pmul(cc2, pr(F1[0], F2[0]))));
+        const int r = opp(q);
+        o[r] = pfma(ca2, pr(fb[r], gb[r]), pfma(cb2, pr(feq[1], geq[1]), pmul(cc2, pr(F1[1], F2[1]))));
     }
 #pragma unroll
     for (int k = 0; k < 6; k++) {
@@ -535,11 +537,17 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const InstDev *__restrict__ i
         const T af = (T(2) * tf - h) * rf, bf = T(3) * h * rf, cf = T(3) * tf * h * rf;
         const PtInv<T> v = pt_inv<T>(I, s);
 #pragma unroll
-        for (int q = 0; q < Q; q++) {
-            T feq, geq, Ff, Fg;
-            eq_src<T>(s, v, q, feq, geq, Ff, Fg);
-            S.bp[q * L::A1 + r] = pfma(pr(af, ag), pr(fv[q], S.sg[q * L::A1 + r]),
-                                       pfma(pr(bf, bg), pr(feq, geq), pmul(pr(cf, cg), pr(Ff, Fg))));
+        for (int k = 0; k < 5; k++) {
+            // the rest direction, then the opposite pairs 1|3, 2|4, 5|7, 6|8
+            const int q = k == 0 ? 0 : k < 3 ? k : k + 2;
+            T feq[2], geq[2], Ff[2], Fg[2];
+            eq_src2<T>(s, v, q, feq, geq, Ff, Fg);
+#pragma unroll
+            for (int e = 0; e < (k == 0 ? 1 : 2); e++) {
+                const int qq = e == 0 ? q : opp(q);
+                S.bp[qq * L::A1 + r] = pfma(pr(af, ag), pr(fv[qq], S.sg[qq * L::A1 + r]),
+                                            pfma(pr(bf, bg), pr(feq[e], geq[e]), pmul(pr(cf, cg), pr(Ff[e], Fg[e]))));
+            }
         }
     }
     __syncthreads();

@@ -66,6 +66,7 @@ struct PtInv {
     T fg;      // phi / (c_s^2 rho)
     T Gx, Gy;  // F - grad p
     T cgx, cgy;  // c_s^2 grad rho
+    T uF, ucg, uG;  // u.F, u.(c_s^2 grad rho), u.(F - grad p)
 };
 
 template <typename T>
@@ -82,6 +83,9 @@ __device__ __forceinline__ PtInv<T> pt_inv_p(const ParT<T> &Pr, const Pt<T> &s)
     v.Gy = s.Fy - s.gpy;
     v.cgx = cs2 * s.grx;
     v.cgy = cs2 * s.gry;
+    v.uF = s.ux * s.Fx + s.uy * s.Fy;
+    v.ucg = s.ux * v.cgx + s.uy * v.cgy;
+    v.uG = s.ux * v.Gx + s.uy * v.Gy;
     return v;
 }
 
@@ -91,20 +95,56 @@ __device__ __forceinline__ PtInv<T> pt_inv(const InstDev &I, const Pt<T> &s)
     return pt_inv_p<T>(par<T>(I), s);
 }
 
-// f^eq_q, g^eq_q (Eqs. feq, geq, su, Hi) and F^f_q, F^g_q (Eqs. F, G)
+// xi_q . (ax, ay) with the zero components of xi_q left out.
+template <typename T>
+__device__ __forceinline__ T xi_dot(int q, T ax, T ay)
+{
+    return cx(q) == 0 ? (cy(q) == 0 ? T(0) : T(cy(q)) * ay)
+                      : (cy(q) == 0 ? T(cx(q)) * ax : T(cx(q)) * ax + T(cy(q)) * ay);
+}
+
+// f^eq, g^eq (Eqs. feq, geq, su, Hi) and F^f, F^g (Eqs. F, G) of direction q
+// (index 0) and of its opposite opp(q) (index 1).  With xi_opp = -xi_q the two
+// share w, (xi.u)^2 and, up to sign, xi.u, xi.F, xi.(c_s^2 grad rho) and
+// xi.(F - grad p); (xi - u).X is formed as xi.X - u.X.  For q = 0 both
+// entries are those of the rest direction.
+template <typename T>
+__device__ __forceinline__ void eq_src2(const Pt<T> &s, const PtInv<T> &v, int q, T (&feq)[2], T (&geq)[2], T (&Ff)[2],
+                                        T (&Fg)[2])
+{
+    const T w = T(wq(q));
+    const T xu = xi_dot<T>(q, s.ux, s.uy);
+    const T a = w * (T(4.5) * (xu * xu) - v.uu15);   // even part of s_i
+    const T b = T(3.0 * wq(q)) * xu;                 // odd part of s_i
+    const T xF = xi_dot<T>(q, s.Fx, s.Fy), xc = xi_dot<T>(q, v.cgx, v.cgy), xG = xi_dot<T>(q, v.Gx, v.Gy);
+    const T H = (q == 0) ? s.phi - T(1.0 - wq(q)) * v.emu : w * v.emu;
+    const T wp = w * s.p, wsrc = w * v.srcF;
+#pragma unroll
+    for (int k = 0; k < 2; k++) {
+        const T si = k == 0 ? a + b : a - b;
+        feq[k] = wp + v.prho * si;
+        geq[k] = H + s.phi * si;
+        const T G = w + si;
+        const T eF = (k == 0 ? xF : -xF) - v.uF;
+        const T ec = (k == 0 ? xc : -xc) - v.ucg;
+        const T eG = (k == 0 ? xG : -xG) - v.uG;
+        Ff[k] = G * eF + si * ec - wsrc;
+        Fg[k] = v.fg * eG * G;
+    }
+}
+
+// The same for one direction q; bit for bit the entry that eq_src2 gives for q.
 template <typename T>
 __device__ __forceinline__ void eq_src(const Pt<T> &s, const PtInv<T> &v, int q, T &feq, T &geq, T &Ff, T &Fg)
 {
-    const T w = T(wq(q));
-    const T xu = T(cx(q)) * s.ux + T(cy(q)) * s.uy;
-    const T si = w * (T(3) * xu + T(4.5) * xu * xu - v.uu15);
-    feq = w * s.p + v.prho * si;
-    const T H = (q == 0) ? s.phi - (T(1) - w) * v.emu : w * v.emu;
-    geq = H + s.phi * si;
-    const T G = w + si;
-    const T ex = T(cx(q)) - s.ux, ey = T(cy(q)) - s.uy;
-    Ff = ex * (s.Fx * G + si * v.cgx) + ey * (s.Fy * G + si * v.cgy) - w * v.srcF;
-    Fg = v.fg * (ex * v.Gx + ey * v.Gy) * G;
+    const bool base = q == 0 || q == 1 || q == 2 || q == 5 || q == 6;
+    T e[2], g[2], f1[2], f2[2];
+    eq_src2<T>(s, v, base ? q : opp(q), e, g, f1, f2);
+    const int k = base ? 0 : 1;
+    feq = e[k];
+    geq = g[k];
+    Ff = f1[k];
+    Fg = f2[k];
 }
 
 // compatibility wrapper: equilibria and sources of one direction

@@ -283,11 +283,17 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
             const T af = (T(2) * tf - h) * rf, bf = T(3) * h * rf, cf = T(3) * tf * h * rf;
             const PtInv<T> v = pt_inv<T>(I, s);
 #pragma unroll
-            for (int q = 0; q < Q; q++) {
-                T feq, geq, Ff, Fg;
-                eq_src<T>(s, v, q, feq, geq, Ff, Fg);
-                S.bp[q * L::A1 + k1] = pfma(pr(af, ag), pr(fv[q], gr[q * SL::GROWS * L::W1]),
-                                            pfma(pr(bf, bg), pr(feq, geq), pmul(pr(cf, cg), pr(Ff, Fg))));
+            for (int k = 0; k < 5; k++) {
+                // the rest direction, then the opposite pairs 1|3, 2|4, 5|7, 6|8
+                const int q = k == 0 ? 0 : k < 3 ? k : k + 2;
+                T feq[2], geq[2], Ff[2], Fg[2];
+                eq_src2<T>(s, v, q, feq, geq, Ff, Fg);
+#pragma unroll
+                for (int e = 0; e < (k == 0 ? 1 : 2); e++) {
+                    const int qq = e == 0 ? q : opp(q);
+                    S.bp[qq * L::A1 + k1] = pfma(pr(af, ag), pr(fv[qq], gr[qq * SL::GROWS * L::W1]),
+                                                 pfma(pr(bf, bg), pr(feq[e], geq[e]), pmul(pr(cf, cg), pr(Ff[e], Fg[e]))));
+                }
             }
         }
         __syncthreads();
