@@ -264,9 +264,10 @@ void harvest_events(dugks_sim *s)
 }
 
 // Resident CTAs per SM that the registers of a fused-step instantiation are
-// sized for (shared memory allows the same count).
+// sized for.  The 288-thread strips take 2: at 96 registers they do not spill,
+// and they run faster than 3 resident strips held to 72 registers.
 template <typename T, int NT, bool SEP>
-constexpr int fused_minb() { return sizeof(T) == 8 ? 1 : (SEP || NT > 288 ? 2 : NT <= 128 ? 4 : 3); }
+constexpr int fused_minb() { return sizeof(T) == 8 ? 1 : (SEP || NT >= 288 ? 2 : NT <= 128 ? 4 : 3); }
 
 template <typename T, int BX, int BY, int NT, bool SEP>
 int prepare_shape()
@@ -930,6 +931,13 @@ int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *para
             P.muA = (U)I.muA; P.muB = (U)I.muB; P.lambda = (U)I.lambda; P.tau_g = (U)I.tau_g;
             P.beta = (U)I.beta; P.kappa = (U)I.kappa; P.gxa = (U)I.gxa; P.gya = (U)I.gya; P.rho_ref = (U)I.rho_ref;
             P.dt = (U)I.dt; P.h = (U)I.h; P.eta = (U)I.eta; P.gamma = (U)I.gamma; P.drho = (U)I.drho;
+            const double K = I.muA * I.muB * (I.phiA - I.phiB), tg = I.tau_g;
+            P.hmuA = (U)(I.h * I.muA); P.hmuB = (U)(I.h * I.muB);
+            P.k6 = (U)(6.0 * K); P.k3h = (U)(3.0 * K * I.h); P.k9h = (U)(9.0 * K * I.h);
+            P.gfa = (U)(2.0 * tg / (2.0 * tg + I.h)); P.gfb = (U)(I.h / (2.0 * tg + I.h));
+            P.gfc = (U)(tg * I.h / (2.0 * tg + I.h));
+            P.gca = (U)((2.0 * tg - I.h) / (2.0 * tg + I.dt)); P.gcb = (U)(3.0 * I.h / (2.0 * tg + I.dt));
+            P.gcc = (U)(3.0 * tg * I.h / (2.0 * tg + I.dt));
         };
         fill(I.pd);
         fill(I.pf);

@@ -184,12 +184,11 @@ __device__ __forceinline__ void face_tail(const InstDev &I, const T (&fb)[Q], co
     s.lapmu = ax.lapmu;
     s.gpx = ax.gpx;
     s.gpy = ax.gpy;
-    const T tf = tauf_of<T>(I, phi, s.rho), tg = Pr.tau_g;
     const PtInv<T> v = pt_inv<T>(I, s);
-    const T r1 = fdiv(T(1), T(2) * tf + h), r2 = fdiv(T(1), T(2) * tg + h);
-    const T a1 = T(2) * tf * r1, b1 = h * r1, c1 = tf * h * r1;
-    const T a2 = T(2) * tg * r2, b2 = h * r2, c2 = tg * h * r2;
-    const pair_t<T> ca2 = pr(a1, a2), cb2 = pr(b1, b2), cc2 = pr(c1, c2);
+    T a1, b1, c1;
+    face_weights<T>(Pr, phi, s.rho, a1, b1, c1);
+    const T tg = Pr.tau_g, r2 = fdiv(T(1), T(2) * tg + h);   // the g weights, formed here: fewer live registers
+    const pair_t<T> ca2 = pr(a1, T(2) * tg * r2), cb2 = pr(b1, h * r2), cc2 = pr(c1, tg * h * r2);
     pair_t<T> o[Q];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
@@ -482,9 +481,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const InstDev *__restrict__ i
     __syncthreads();
 
     // ---- phase 4: grad p, u and bar-plus of both distributions on R1 (Eq. relations1)
-    const T dt = Pr.dt, h = Pr.h, tg = Pr.tau_g;
-    const T rg = fdiv(T(1), T(2) * tg + dt);
-    const T ag = (T(2) * tg - h) * rg, bg = T(3) * h * rg, cg = T(3) * tg * h * rg;
+    const T dt = Pr.dt, h = Pr.h;
+    const T ag = Pr.gca, bg = Pr.gcb, cg = Pr.gcc;
     for (int r = tid; r < L::A1; r += NT) {
         const int x = r % L::W1 - 1, y = r / L::W1 - 1;
         if (!S.ok(0, x) || !S.ok(1, y)) {
@@ -532,9 +530,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const InstDev *__restrict__ i
         s.gry = Pr.drho * gfy;
         s.gpx = gpx;
         s.gpy = gpy;
-        const T tf = tauf_of<T>(I, s.phi, s.rho);
-        const T rf = fdiv(T(1), T(2) * tf + dt);
-        const T af = (T(2) * tf - h) * rf, bf = T(3) * h * rf, cf = T(3) * tf * h * rf;
+        T af, bf, cf;
+        cell_weights<T>(Pr, s.phi, s.rho, af, bf, cf);
         const PtInv<T> v = pt_inv<T>(I, s);
 #pragma unroll
         for (int k = 0; k < 5; k++) {

@@ -49,6 +49,32 @@ __device__ __forceinline__ T tauf_of(const InstDev &I, T phi, T rho)
     return fdiv(T(3) * mu, rho);
 }
 
+// Weights of the f relaxation with tau_f = 3K/(D rho) (Eq. mixvis and
+// Eq. kineticandmobility; K = muA muB (phiA - phiB), D = (phi - phiB) muB +
+// (phiA - phi) muA).  At a face (Eq. relations2 with h): 2tau/(2tau + h),
+// h/(2tau + h), tau h/(2tau + h), which are 6K, X and 3Kh over 6K + X with
+// X = h D rho.  At a cell (Eq. relations1): (2tau - h)/(2tau + dt),
+// 3h/(2tau + dt), 3 tau h/(2tau + dt), which are 6K - X, 3X and 9Kh over
+// 6K + 2X.  One reciprocal per point.
+template <typename T>
+__device__ __forceinline__ void face_weights(const ParT<T> &Pr, T phi, T rho, T &a, T &b, T &c)
+{
+    const T X = ((phi - Pr.phiB) * Pr.hmuB + (Pr.phiA - phi) * Pr.hmuA) * rho;
+    const T r = fdiv(T(1), Pr.k6 + X);
+    a = Pr.k6 * r;
+    b = X * r;
+    c = Pr.k3h * r;
+}
+template <typename T>
+__device__ __forceinline__ void cell_weights(const ParT<T> &Pr, T phi, T rho, T &a, T &b, T &c)
+{
+    const T X = ((phi - Pr.phiB) * Pr.hmuB + (Pr.phiA - phi) * Pr.hmuA) * rho;
+    const T r = fdiv(T(1), Pr.k6 + T(2) * X);
+    a = (Pr.k6 - X) * r;
+    b = T(3) * X * r;
+    c = Pr.k9h * r;
+}
+
 // Point state from which equilibria and sources follow.
 template <typename T>
 struct Pt {

@@ -30,8 +30,8 @@ struct StripLayout {
     static constexpr size_t st_g = sizeof(T) * Q * GROWS * L::W1;
     static constexpr size_t st_flux = sizeof(pair_t<T>) * 6 * NFT;
     static constexpr size_t un = (st_f + st_g > st_flux) ? st_f + st_g : st_flux;
-    static constexpr size_t o_keep = al(o_un + un);       // carried y-face row [6][BX] pairs
-    static constexpr size_t bytes = al(o_keep + sizeof(pair_t<T>) * 6 * BX);
+    static constexpr size_t o_keep = al(o_un + un);       // carried y-face rows [2][6][BX] pairs (by block parity)
+    static constexpr size_t bytes = al(o_keep + sizeof(pair_t<T>) * 2 * 6 * BX);
 };
 
 template <typename T, int BX, int BY, int NT, int MINB, bool UNI>
@@ -47,7 +47,9 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
     T *stf = (T *)(smem + SL::o_un);                      // staged tilde f [Q][FROWS][W2]
     T *stg = stf + Q * SL::FROWS * L::W2;                 // staged tilde g [Q][GROWS][W1]
     pair_t<T> *flux = (pair_t<T> *)(smem + SL::o_un);    // [6][NFT], reuses the staging bytes
-    pair_t<T> *keep = (pair_t<T> *)(smem + SL::o_keep);  // [6][BX]: the bottom y faces of the block
+    // two [6][BX] buffers: block b reads its bottom y faces from buffer b % 2
+    // and leaves its top y faces, the next block's bottom ones, in the other
+    pair_t<T> *const keep0 = (pair_t<T> *)(smem + SL::o_keep);
     const int4 t = chunks[blockIdx.x];
     const InstDev &I = insts[t.x];
     const ParT<T> &Pr = par<T>(I);
@@ -74,9 +76,8 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
         }
     }
     const T cs2 = Cst<T>::cs2;
-    const T hdt = T(0.5) * Pr.dt, dt = Pr.dt, h = Pr.h, tg = Pr.tau_g;
-    const T rg = fdiv(T(1), T(2) * tg + dt);
-    const T ag = (T(2) * tg - h) * rg, bg = T(3) * h * rg, cg = T(3) * tg * h * rg;
+    const T hdt = T(0.5) * Pr.dt, dt = Pr.dt;
+    const T ag = Pr.gca, bg = Pr.gcb, cg = Pr.gcc;
     // global index of a column (x) or of row y of block b (wrapped on a periodic
     // axis, -1 outside the domain)
     auto gwrap = [&](bool isx, int g) -> int {
@@ -118,10 +119,9 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
     }
     __syncthreads();
 
-    // rows of block b: phi [ph0, ph1) into the phi ring, tilde f rows [fr0, fr1)
-    // and tilde g rows [gr0, gr1) into the staging area (zero outside the
-    // domain), and the geometry of the rows [4, BY + 4) that are new to it
-    auto load_rows = [&](int b, int ph0, int ph1, int fr0, int fr1, int gr0, int gr1) {
+    // rows of block b: phi [ph0, ph1) into the phi ring and the geometry of
+    // the rows [4, BY + 4) that are new to it
+    auto load_phi = [&](int b, int ph0, int ph1) {
         if (b >= 0)
             for (int r = tid; r < BY; r += NT) set_geo(L::W4 + 8 + r, false, 4 + r, grow(b, 4 + r));
         const int bb = b < 0 ? 0 : b;
@@ -136,6 +136,11 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
                 S.phi[TL::i4(x, y)] = z;
             }
         }
+    };
+    // tilde f rows [fr0, fr1) and tilde g rows [gr0, gr1) of block b into the
+    // staging area (zero outside the domain)
+    auto load_fg = [&](int b, int fr0, int fr1, int gr0, int gr1) {
+        const int bb = b < 0 ? 0 : b;
         for (int r = tid; r < (fr1 - fr0) * L::W2; r += NT) {
             const int x = r % L::W2 - 2, yy = r / L::W2;
             const int gi = S.gidx(0, x), gj = grow(bb, fr0 + yy);
@@ -162,6 +167,8 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
                 for (int q = 0; q < Q; q++) d[q * SL::GROWS * L::W1] = T(0);
             }
         }
+    };
+    auto load_wait = [&]() {
         cp_commit();
         cp_wait<0>();
         __syncthreads();
@@ -278,9 +285,8 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
             s.gry = Pr.drho * gfy;
             s.gpx = gpx;
             s.gpy = gpy;
-            const T tf = tauf_of<T>(I, s.phi, s.rho);
-            const T rf = fdiv(T(1), T(2) * tf + dt);
-            const T af = (T(2) * tf - h) * rf, bf = T(3) * h * rf, cf = T(3) * tf * h * rf;
+            T af, bf, cf;
+            cell_weights<T>(Pr, s.phi, s.rho, af, bf, cf);
             const PtInv<T> v = pt_inv<T>(I, s);
 #pragma unroll
             for (int k = 0; k < 5; k++) {
@@ -300,15 +306,20 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
     };
 
     // ---- prologue: the bottom rows of the first block's rings
-    load_rows(-1, -4, 4, -2, 2, -1, 1);
+    load_phi(-1, -4, 4);
+    load_fg(-1, -2, 2, -1, 1);
+    load_wait();
     mu_rows(-3, 3);
     p_rows(-2, 2, -2);
     r1_rows(-1, 1, -2, -1);
 
     const int x = tid % BX, y = tid / BX;
     for (int b = 0; b < nblk; b++) {
-        // ---- the new rows of every region
-        load_rows(b, 4, BY + 4, 1, BY + 2, 1, BY + 1);
+        // ---- the new rows of every region (the staged tilde rows of a later
+        // block were issued before the shift that ended the previous block)
+        load_phi(b, 4, BY + 4);
+        if (b == 0) load_fg(0, 1, BY + 2, 1, BY + 1);
+        load_wait();
         mu_rows(3, BY + 3);
         p_rows(2, BY + 2, 1);
         r1_rows(1, BY + 1, 1, 1);
@@ -321,10 +332,14 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
             if (k < L::NFX) tile_face<T, 0, UNI>(I, S, k % (BX + 1) - 1, k / (BX + 1), F2o);
             else if (k < SL::NFT) tile_face<T, 1, UNI>(I, S, (k - L::NFX) % BX, (k - L::NFX) / BX, F2o);
             else tile_face<T, 1, UNI>(I, S, k - SL::NFT, -1, F2o);
-            pair_t<T> *dst = k < SL::NFT ? flux + k : keep + (k - SL::NFT);
+            pair_t<T> *dst = k < SL::NFT ? flux + k : keep0 + (k - SL::NFT);   // block 0: buffer 0
             const int stride = k < SL::NFT ? SL::NFT : BX;
 #pragma unroll
             for (int m = 0; m < 6; m++) dst[m * stride] = F2o[m];
+            if (k >= SL::NFT - BX && k < SL::NFT) {   // top row: also the next block's bottom faces
+#pragma unroll
+                for (int m = 0; m < 6; m++) keep0[((b + 1) & 1) * 6 * BX + m * BX + (k - (SL::NFT - BX))] = F2o[m];
+            }
         }
         __syncthreads();
         // ---- update of the block's cell (Eqs. relations2, updatef)
@@ -338,7 +353,7 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
 #pragma unroll
             for (int m = 0; m < 6; m++) {
                 const int qx = xset(m), qy = yset(m);
-                const pair_t<T> south = (y == 0) ? keep[m * BX + x] : flux[m * SL::NFT + kn - BX];
+                const pair_t<T> south = (y == 0) ? keep0[(b & 1) * 6 * BX + m * BX + x] : flux[m * SL::NFT + kn - BX];
                 J[qx] = padd(J[qx], psub(flux[m * SL::NFT + ke], flux[m * SL::NFT + kw]));
                 J[qy] = padd(J[qy], psub(flux[m * SL::NFT + kn], south));
             }
@@ -383,12 +398,15 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
         }
         __syncthreads();
         if (b + 1 == nblk) break;
-        // ---- carry the top y faces and shift the shared ring rows and their
-        // geometry down by BY (a uniform instance keeps its one row record).
-        // The rows of a ring are contiguous and 16-byte aligned, so they move
-        // in 16-byte words: one pass over all the segments.
+        // ---- issue the next block's staged tilde rows (the staging bytes are
+        // free once the update has read the fluxes), then shift the shared ring
+        // rows and their geometry down by BY while they are in flight (a uniform
+        // instance keeps its one row record).  The rows of a ring are contiguous
+        // and 16-byte aligned, so they move in 16-byte words: one pass over all
+        // the segments.
+        load_fg(b + 1, 1, BY + 2, 1, BY + 1);
+        cp_commit();
         {
-            constexpr int KB = (int)(sizeof(pair_t<T>) * BX / 16);              // carried faces, per direction
             constexpr int PHB = (int)(sizeof(phi_t<T>) * 8 * L::W4 / 16);
             constexpr int MUB = (int)(sizeof(T) * 6 * L::W3 / 16);
             constexpr int PB = (int)(sizeof(T) * 4 * L::W2 / 16);
@@ -401,18 +419,14 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
                               sizeof(T) * BY * L::W1 % 16 == 0 && sizeof(pair_t<T>) * SL::NFT % 16 == 0 &&
                               sizeof(pair_t<T>) * (L::NFX + (BY - 1) * BX) % 16 == 0,
                           "16-byte ring rows");
-            constexpr int NKEEP = 6 * KB, NPHI = NKEEP + PHB, NMU = NPHI + MUB, NP = NMU + PB, NAUX = NP + 7 * AB;
+            constexpr int NPHI = PHB, NMU = NPHI + MUB, NP = NMU + PB, NAUX = NP + 7 * AB;
             constexpr int NALL = NAUX + Q * BB;
             for (int k = tid; k < NALL; k += NT) {
                 float4 *d;
                 const float4 *src;
-                if (k < NKEEP) {
-                    const int m = k / KB, w = k % KB;
-                    d = (float4 *)(keep + m * BX) + w;
-                    src = (const float4 *)(flux + m * SL::NFT + L::NFX + (BY - 1) * BX) + w;
-                } else if (k < NPHI) {
-                    d = (float4 *)S.phi + (k - NKEEP);
-                    src = (const float4 *)(S.phi + BY * L::W4) + (k - NKEEP);
+                if (k < NPHI) {
+                    d = (float4 *)S.phi + k;
+                    src = (const float4 *)(S.phi + BY * L::W4) + k;
                 } else if (k < NMU) {
                     d = (float4 *)S.mu + (k - NPHI);
                     src = (const float4 *)(S.mu + BY * L::W3) + (k - NPHI);
