@@ -12,6 +12,12 @@
 // grow with the strip length.  The thread count NT is chosen so that the new
 // rows of a phase fill whole passes of the threads (with BX = 32, BY = 8 and
 // 288 threads: p 288 items, bar-plus 272, faces 520 in two passes).
+//
+// Loads of a later block overlap the work of the one before: its new phi rows
+// are copied into a staging area while the faces and the update run, and its
+// tilde f and g rows into the (then free) flux bytes while the rings shift.
+// The shift refills the phi rows it moves down from the staging area, so a
+// block starts without a load wait of its own.
 #pragma once
 #include "dugks_fused.cuh"
 
@@ -20,7 +26,7 @@ namespace dugks {
 template <typename T, int BX, int BY>
 struct StripLayout {
     using L = FusedLayout<T, BX, BY, false>;
-    static_assert(BY >= 8, "the shifted ring rows must not overlap the new rows");
+    static_assert(BY == 8, "the shifted ring rows are the rows that the next block's new rows replace");
     static constexpr int NFY = BX * BY;                   // y faces per block (the bottom row is carried)
     static constexpr int NFT = L::NFX + NFY;
     static constexpr int FROWS = BY + 1, GROWS = BY;      // staged tilde rows of a block (f: 1..BY+1, g: 1..BY)
@@ -30,7 +36,9 @@ struct StripLayout {
     static constexpr size_t st_g = sizeof(T) * Q * GROWS * L::W1;
     static constexpr size_t st_flux = sizeof(pair_t<T>) * 6 * NFT;
     static constexpr size_t un = (st_f + st_g > st_flux) ? st_f + st_g : st_flux;
-    static constexpr size_t o_keep = al(o_un + un);       // carried y-face rows [2][6][BX] pairs (by block parity)
+    static constexpr size_t o_st = o_un;                  // staging: the flux bytes, free after the update
+    static constexpr size_t o_phst = al(o_un + un);  // the next block's new phi rows [BY][W4]
+    static constexpr size_t o_keep = al(o_phst + sizeof(phi_t<T>) * BY * L::W4);      // carried y-face rows [2][6][BX] pairs (by block parity)
     static constexpr size_t bytes = al(o_keep + sizeof(pair_t<T>) * 2 * 6 * BX);
 };
 
@@ -44,9 +52,10 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
     using TL = Tile<T, BX, BY, UNI, false>;
     extern __shared__ __align__(16) unsigned char smem[];
     TL S(smem);
-    T *stf = (T *)(smem + SL::o_un);                      // staged tilde f [Q][FROWS][W2]
+    T *stf = (T *)(smem + SL::o_st);                      // staged tilde f [Q][FROWS][W2]
     T *stg = stf + Q * SL::FROWS * L::W2;                 // staged tilde g [Q][GROWS][W1]
-    pair_t<T> *flux = (pair_t<T> *)(smem + SL::o_un);    // [6][NFT], reuses the staging bytes
+    phi_t<T> *phst = (phi_t<T> *)(smem + SL::o_phst);    // staged phi rows 4 .. BY + 3 of the next block
+    pair_t<T> *flux = (pair_t<T> *)(smem + SL::o_un);    // [6][NFT]
     // two [6][BX] buffers: block b reads its bottom y faces from buffer b % 2
     // and leaves its top y faces, the next block's bottom ones, in the other
     pair_t<T> *const keep0 = (pair_t<T> *)(smem + SL::o_keep);
@@ -134,6 +143,20 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
                 phi_t<T> z;
                 phi_from_zero(z);
                 S.phi[TL::i4(x, y)] = z;
+            }
+        }
+    };
+    // the new phi rows 4 .. BY + 3 of block b into the phi staging rows
+    auto load_phi_next = [&](int b) {
+        for (int r = tid; r < BY * L::W4; r += NT) {
+            const int x = r % L::W4 - 4, y = 4 + r / L::W4;
+            const int gi = S.gidx(0, x), gj = grow(b, y);
+            if (UNI || (gi >= 0 && gj >= 0)) {
+                cp_async<sizeof(phi_t<T>)>(phst + r, io.phi_in + cell(gi, gj));
+            } else {
+                phi_t<T> z;
+                phi_from_zero(z);
+                phst[r] = z;
             }
         }
     };
@@ -315,14 +338,21 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
 
     const int x = tid % BX, y = tid / BX;
     for (int b = 0; b < nblk; b++) {
-        // ---- the new rows of every region (the staged tilde rows of a later
-        // block were issued before the shift that ended the previous block)
-        load_phi(b, 4, BY + 4);
-        if (b == 0) load_fg(0, 1, BY + 2, 1, BY + 1);
-        load_wait();
+        // ---- the new rows of every region; those of a later block were
+        // loaded during the block before
+        if (b == 0) {
+            load_phi(0, 4, BY + 4);
+            load_fg(0, 1, BY + 2, 1, BY + 1);
+            load_wait();
+        }
         mu_rows(3, BY + 3);
         p_rows(2, BY + 2, 1);
         r1_rows(1, BY + 1, 1, 1);
+        // the next block's new phi rows land while the faces and the update run
+        if (b + 1 < nblk) {
+            load_phi_next(b + 1);
+            cp_commit();
+        }
         // ---- faces: x faces of the block rows and y faces 0|1 .. BY-1|BY; the
         // first block also forms its bottom faces -1|0 (a wall face there
         // differences bar-plus up to row 1); later blocks carry them over
@@ -396,14 +426,15 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
             }
             if (!finite) atomicOr(io.status + t.x, ST_NONFINITE);
         }
+        cp_wait<0>();   // the next block's phi rows are in; the barrier makes them visible
         __syncthreads();
         if (b + 1 == nblk) break;
-        // ---- issue the next block's staged tilde rows (the staging bytes are
-        // free once the update has read the fluxes), then shift the shared ring
-        // rows and their geometry down by BY while they are in flight (a uniform
-        // instance keeps its one row record).  The rows of a ring are contiguous
-        // and 16-byte aligned, so they move in 16-byte words: one pass over all
-        // the segments.
+        // ---- the next block's tilde rows into the staging bytes (free once the
+        // update has read the fluxes); while they are in flight, shift the
+        // shared ring rows and their geometry down by BY (a uniform instance
+        // keeps its one row record) and write the new rows' phi and geometry.
+        // The rows of a ring are contiguous and 16-byte aligned, so they move
+        // in 16-byte words: one pass over all the segments.
         load_fg(b + 1, 1, BY + 2, 1, BY + 1);
         cp_commit();
         {
@@ -425,8 +456,12 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
                 float4 *d;
                 const float4 *src;
                 if (k < NPHI) {
-                    d = (float4 *)S.phi + k;
-                    src = (const float4 *)(S.phi + BY * L::W4) + k;
+                    // the thread that moves a word down also refills it with the
+                    // next block's staged row
+                    float4 *up = (float4 *)(S.phi + BY * L::W4) + k;
+                    ((float4 *)S.phi)[k] = *up;
+                    *up = ((const float4 *)phst)[k];
+                    continue;
                 } else if (k < NMU) {
                     d = (float4 *)S.mu + (k - NPHI);
                     src = (const float4 *)(S.mu + BY * L::W3) + (k - NPHI);
@@ -452,7 +487,10 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
 #pragma unroll
                 for (int k = 0; k < 11; k++) S.ga[k * L::NG + L::W4 + r] = S.ga[k * L::NG + L::W4 + BY + r];
             }
+            // the same thread then writes the geometry of the next block's new row r
+            set_geo(L::W4 + 8 + r, false, 4 + r, grow(b + 1, 4 + r));
         }
+        cp_wait<0>();   // the next block's tilde rows are in
         __syncthreads();
     }
 }
