@@ -581,7 +581,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const InstDev *__restrict__ i
         }
     }
     const int r1 = TL::i1(x, y);
-    const T dtv = dt / (S.c(10, 0, x) * S.c(10, 1, y));
+    const T dtv = fdiv(dt, S.c(10, 0, x) * S.c(10, 1, y));
     // tilde^{n+1} = 4/3 bar-plus - 1/3 tilde - dt/|V| J
     pair_t<T> nw[Q];
     const int r2 = TL::i2(x, y);

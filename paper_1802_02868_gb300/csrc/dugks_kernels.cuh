@@ -21,10 +21,13 @@ struct Cst {
 };
 
 // a / b: IEEE division in FP64 mode; in FP32 mode the fast reciprocal-based
-// division (within 2 ulp), used only for 1/rho, 1/(2 tau + dt) and the mixed
-// viscosity, all well away from overflow.
+// division (within 2 ulp), used only for 1/rho, the relaxation weights, the
+// mixed viscosity and dt/|V|, all well away from overflow.
 __device__ __forceinline__ double fdiv(double a, double b) { return a / b; }
 __device__ __forceinline__ float fdiv(float a, float b) { return __fdividef(a, b); }
+// a * b + c with one rounding
+__device__ __forceinline__ double tfma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float tfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
 __device__ __forceinline__ long long cell_of(const InstDev &I, int i, int j)
 {
@@ -140,7 +143,7 @@ __device__ __forceinline__ void eq_src2(const Pt<T> &s, const PtInv<T> &v, int q
 {
     const T w = T(wq(q));
     const T xu = xi_dot<T>(q, s.ux, s.uy);
-    const T a = w * (T(4.5) * (xu * xu) - v.uu15);   // even part of s_i
+    const T a = tfma(T(4.5 * wq(q)), xu * xu, -(w * v.uu15));   // even part of s_i
     const T b = T(3.0 * wq(q)) * xu;                 // odd part of s_i
     const T xF = xi_dot<T>(q, s.Fx, s.Fy), xc = xi_dot<T>(q, v.cgx, v.cgy), xG = xi_dot<T>(q, v.Gx, v.Gy);
     const T H = (q == 0) ? s.phi - T(1.0 - wq(q)) * v.emu : w * v.emu;
@@ -154,7 +157,7 @@ __device__ __forceinline__ void eq_src2(const Pt<T> &s, const PtInv<T> &v, int q
         const T eF = (k == 0 ? xF : -xF) - v.uF;
         const T ec = (k == 0 ? xc : -xc) - v.ucg;
         const T eG = (k == 0 ? xG : -xG) - v.uG;
-        Ff[k] = G * eF + si * ec - wsrc;
+        Ff[k] = tfma(G, eF, tfma(si, ec, -wsrc));
         Fg[k] = v.fg * eG * G;
     }
 }

@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
             }
             const long long c = cell(gi, gj);
             const int r1 = TL::i1(x, y);
-            const T dtv = dt / (S.c(10, 0, x) * S.c(10, 1, y));
+            const T dtv = fdiv(dt, S.c(10, 0, x) * S.c(10, 1, y));
             pair_t<T> nw[Q];
 #pragma unroll
             for (int q = 0; q < Q; q++)
