@@ -934,8 +934,6 @@ int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *para
             const double K = I.muA * I.muB * (I.phiA - I.phiB), tg = I.tau_g;
             P.hmuA = (U)(I.h * I.muA); P.hmuB = (U)(I.h * I.muB);
             P.k6 = (U)(6.0 * K); P.k3h = (U)(3.0 * K * I.h); P.k9h = (U)(9.0 * K * I.h);
-            P.gfa = (U)(2.0 * tg / (2.0 * tg + I.h)); P.gfb = (U)(I.h / (2.0 * tg + I.h));
-            P.gfc = (U)(tg * I.h / (2.0 * tg + I.h));
             P.gca = (U)((2.0 * tg - I.h) / (2.0 * tg + I.dt)); P.gcb = (U)(3.0 * I.h / (2.0 * tg + I.dt));
             P.gcc = (U)(3.0 * tg * I.h / (2.0 * tg + I.dt));
         };

@@ -86,11 +86,10 @@ struct ParT {
     T phiA, phiB, rhoA, rhoB, muA, muB, lambda, tau_g, beta, kappa, gxa, gya, rho_ref;
     T dt, h, eta, gamma, drho;
     // relaxation weights: with K = muA muB (phiA - phiB), h muA, h muB and the
-    // numerators 6K, 3Kh, 9Kh of the f weights; the g weights of a face
-    // (2 tau_g, h, tau_g h over 2 tau_g + h) and of a cell (2 tau_g - h, 3h,
-    // 3 tau_g h over 2 tau_g + dt)
+    // numerators 6K, 3Kh, 9Kh of the f weights; the g weights of a cell
+    // (2 tau_g - h, 3h, 3 tau_g h over 2 tau_g + dt)
     T hmuA, hmuB, k6, k3h, k9h;
-    T gfa, gfb, gfc, gca, gcb, gcc;
+    T gca, gcb, gcc;
 };
 
 // A constant of the phi storage: the double and its float pair (hi, lo).

@@ -187,7 +187,9 @@ __device__ __forceinline__ void face_tail(const InstDev &I, const T (&fb)[Q], co
     const PtInv<T> v = pt_inv<T>(I, s);
     T a1, b1, c1;
     face_weights<T>(Pr, phi, s.rho, a1, b1, c1);
-    const T tg = Pr.tau_g, r2 = fdiv(T(1), T(2) * tg + h);   // the g weights, formed here: fewer live registers
+    // the g weights (Eq. original-function with h), formed here rather than
+    // loaded, which keeps fewer values live
+    const T tg = Pr.tau_g, r2 = fdiv(T(1), T(2) * tg + h);
     const pair_t<T> ca2 = pr(a1, T(2) * tg * r2), cb2 = pr(b1, h * r2), cc2 = pr(c1, tg * h * r2);
     pair_t<T> o[Q];
 #pragma unroll
@@ -481,7 +483,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const InstDev *__restrict__ i
     __syncthreads();
 
     // ---- phase 4: grad p, u and bar-plus of both distributions on R1 (Eq. relations1)
-    const T dt = Pr.dt, h = Pr.h;
+    const T dt = Pr.dt;
     const T ag = Pr.gca, bg = Pr.gcb, cg = Pr.gcc;
     for (int r = tid; r < L::A1; r += NT) {
         const int x = r % L::W1 - 1, y = r / L::W1 - 1;
