@@ -423,7 +423,11 @@ def main():
     if kname == "k_step" and prec == dugks.FP32 and kernel_sources_sha() == TRAFFIC_SOURCES_SHA \
             and tuned[1] in TRAFFIC_BYTES_PER_CELL_FP32:
         traffic = TRAFFIC_BYTES_PER_CELL_FP32[tuned[1]] * ncells
-    roof = {"bound": "alu", "kernel": kname, "achieved": tflops, "peak": peak_alu, "unit": "TFLOP/s",
+    # the library times the fused step under one slot, "k_step"; the kernel
+    # behind it is k_strip for the strip shapes
+    kernel = ("k_strip" if "strip" in tuned[1] else "k_step") if kname == "k_step" else kname
+    roof = {"bound": "alu", "kernel": kernel, "timer": kname, "shape": tuned[1], "achieved": tflops, "peak": peak_alu,
+            "unit": "TFLOP/s",
             "frac": tflops / peak_alu, "peak_source": "unit counts x 2.07 GHz max SM clock (%s)" % (
                 "FP32 FMA lanes" if prec == dugks.FP32 else "FP64 DFMA rate"),
             "flop_per_cell": FLOP_PER_CELL_UPDATE, "traffic": traffic, "avg_launch_ms": avg_s * 1e3,
