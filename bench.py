@@ -426,10 +426,16 @@ def main():
     # the library times the fused step under one slot, "k_step"; the kernel
     # behind it is k_strip for the strip shapes
     kernel = ("k_strip" if "strip" in tuned[1] else "k_step") if kname == "k_step" else kname
+    # the same peak measured on this GPU by FMA-only kernels (scalar, packed
+    # two-lane and FP64), after the timed regions
+    meas = dugks.measure_alu_peaks(stream=stream.cuda_stream)
+    peak_meas = max(meas["fp32"], meas["fp32x2"]) if prec == dugks.FP32 else meas["fp64"]
     roof = {"bound": "alu", "kernel": kernel, "timer": kname, "shape": tuned[1], "achieved": tflops, "peak": peak_alu,
             "unit": "TFLOP/s",
             "frac": tflops / peak_alu, "peak_source": "unit counts x 2.07 GHz max SM clock (%s)" % (
                 "FP32 FMA lanes" if prec == dugks.FP32 else "FP64 DFMA rate"),
+            "peak_measured": peak_meas, "frac_of_measured": tflops / peak_meas,
+            "measured_fma_tflops": meas,
             "flop_per_cell": FLOP_PER_CELL_UPDATE, "traffic": traffic, "avg_launch_ms": avg_s * 1e3,
             "hbm": {"achieved": hbm_achieved, "peak": peak_hbm, "unit": "GB/s", "frac": hbm_achieved / peak_hbm,
                     "peak_source": peak_kind, "algorithmic_bytes_per_cell": bpc},

@@ -248,6 +248,18 @@ int dugks_laplace_pressure(dugks_sim *sim, double *P);
 
 const char *dugks_status_str(int status);
 
+/* Arithmetic throughput of the current device, for roofline accounting of the
+   fused step.  The paper has no counterpart.  Runs three FMA-only kernels on
+   cuda_stream (8 blocks of 256 threads per SM, 8 independent FMA chains per
+   thread): FP32 scalar FMAs for iters_f32 rounds, FP32 packed two-lane FMAs
+   (the form the step uses for its f/g pairs) for iters_f32 / 2 rounds, FP64
+   FMAs for iters_f64 rounds.  Each kernel runs twice and the second launch is
+   timed with CUDA events; FMA = 2 flop.  Outputs (host): TFLOP/s of each.
+   Allocates no device memory and writes none; synchronises.  ERR_ARG for
+   iteration counts below 1 or NULL outputs. */
+int dugks_measure_alu_peaks(int iters_f32, int iters_f64, double *fp32_tflops, double *fp32x2_tflops,
+                            double *fp64_tflops, void *cuda_stream);
+
 /* Allocation-free FP64 conservation sums of one mesh.  The paper has no
    counterpart; this exists for callers that cannot allocate device memory,
    such as a host loop under a device-memory budget owned by another allocator

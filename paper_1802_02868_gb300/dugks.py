@@ -120,7 +120,7 @@ EXPORTS = ("dugks_create", "dugks_batch_create", "dugks_destroy", "dugks_init", 
            "dugks_kernel_bytes_per_cell", "dugks_status_str", "dugks_conservation_static",
            "dugks_autotune", "dugks_set_tile_shape", "dugks_tile_shape", "dugks_tile_shape_name",
            "dugks_adjoint", "dugks_uniform_instances", "dugks_diagnostics", "dugks_laplace_pressure",
-           "dugks_batch_set_paused", "dugks_batch_step_each", "dugks_set_allocator")
+           "dugks_batch_set_paused", "dugks_batch_step_each", "dugks_set_allocator", "dugks_measure_alu_peaks")
 STATIC_MAX_CELLS = 16777216
 
 
@@ -170,6 +170,7 @@ def load(build_if_missing: bool = True):
     L.dugks_batch_set_paused.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.dugks_batch_step_each.argtypes = [vp, ctypes.POINTER(ctypes.c_long)]
     L.dugks_set_allocator.argtypes = [ALLOC_FN, FREE_FN, vp]
+    L.dugks_measure_alu_peaks.argtypes = [ip, ip, dp, dp, dp, vp]
     L.dugks_tile_shape_name.argtypes = [ip]
     L.dugks_tile_shape_name.restype = ctypes.c_char_p
     L.dugks_status_str.argtypes = [ip]
@@ -425,6 +426,16 @@ def conservation_static(phi_ptr, dx_ptr, dy_ptr, nx, ny, params, out_ptr, stream
                                             ctypes.c_void_p(int(dy_ptr)), int(nx), int(ny), params.phiA,
                                             params.phiB, params.rhoA, params.rhoB, ctypes.c_void_p(int(out_ptr)),
                                             ctypes.c_void_p(int(stream)))
+
+
+def measure_alu_peaks(iters_f32=262144, iters_f64=4096, stream=0):
+    """FMA throughput of the current device in TFLOP/s (dugks_measure_alu_peaks):
+    a dict with fp32, fp32x2 (packed two-lane FMAs) and fp64."""
+    a, b, c = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check("dugks_measure_alu_peaks", load().dugks_measure_alu_peaks(int(iters_f32), int(iters_f64), ctypes.byref(a),
+                                                                      ctypes.byref(b), ctypes.byref(c),
+                                                                      ctypes.c_void_p(int(stream))))
+    return {"fp32": a.value, "fp32x2": b.value, "fp64": c.value}
 
 
 NUM_TILE_SHAPES = 7
