@@ -188,18 +188,74 @@ def _two_layer_profile(y, H, G, muA, muB):
     return np.where(Y >= 0, uA, uB)
 
 
-@pytest.mark.slow
-@pytest.mark.parametrize("ratio,tol", [(1.0, 0.005), (10.0, 0.05)])
-def test_layered_poiseuille_profile(ratio, tol):
-    """Steady two-layer channel flow on the tanh-refined mesh matches the analytic
-    profile; started from it, the scheme stays within the diffuse-interface error."""
-    H, G = 48.0, 1e-7
-    c = I.layered_poiseuille(nx=2, ny=48, height=H, nu_ratio=ratio, nuB=0.05, force=G)
+def _poiseuille_error(ratio, H, G=1e-7, steps=12000):
+    c = I.layered_poiseuille(nx=2, ny=int(H), height=H, nu_ratio=ratio, nuB=0.05, force=G)
     _, yc = c.mesh.centres()
     ua = _two_layer_profile(yc, H, G, c.params.nuA, c.params.nuB)
     o = oracle.Oracle(c.mesh, c.params).init(c.phi0, ux=np.repeat(ua[:, None], 2, axis=1))
-    o.step(12000)
+    o.step(steps)
     un = o.moments()["ux"][:, 0]
-    assert np.linalg.norm(un - ua) / np.linalg.norm(ua) < tol
-    # and from rest, the centre-line velocity approaches u_c = G Hp^2 / (muA + muB)
-    assert ua[23] == pytest.approx(G * (H / 2) ** 2 / (c.params.nuA + c.params.nuB), rel=0.02)
+    return np.linalg.norm(un - ua) / np.linalg.norm(ua)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("ratio,tol", [(1.0, 0.005), (10.0, 0.05), (100.0, 0.08)])
+def test_layered_poiseuille_profile(ratio, tol):
+    """Steady two-layer channel flow on the tanh-refined mesh (H = 48, interface
+    width 4) matches the analytic profile of Sec. 3.2: started from it, the
+    scheme stays within the diffuse-interface error (measured L2-relative:
+    5e-4 at a viscosity ratio of 1, 0.027 at 10, 0.066 at 100)."""
+    assert _poiseuille_error(ratio, 48.0) < tol
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("ratio", [10.0, 100.0])
+def test_layered_poiseuille_error_falls_with_interface_width(ratio):
+    """The departure from the sharp-interface profile comes from the diffuse
+    interface: doubling the channel at a fixed interface width (W/H halved)
+    cuts it about threefold (measured 0.027 -> 0.009 at ratio 10, 0.066 ->
+    0.022 at ratio 100)."""
+    coarse, fine = _poiseuille_error(ratio, 48.0), _poiseuille_error(ratio, 96.0)
+    assert fine < 0.45 * coarse
+
+
+def _ensemble_like(ratio, bubble, side=64):
+    """A drop or a rising bubble as the batched ensemble draws them (fluid A the
+    light one, rhoB = 1, rhoA = rhoB / ratio, viscosity ratio 10)."""
+    beta, kappa = I.params_from_sigma_width(1e-3, 4.0)
+    rhoB, rhoA, radius = 1.0, 1.0 / ratio, 0.2 * side
+    mesh = I.uniform_mesh(side, side)
+    if bubble:
+        G = 10.0 * 1e-3 / ((rhoB - rhoA) * (2.0 * radius) ** 2)   # Eotvos number 10
+        centre, gy, rho_ref = (0.5 * side, side / 3.0), -G, rhoB
+    else:
+        centre, gy, rho_ref = (0.5 * side, 0.5 * side), 0.0, 0.0
+    prm = I.Params(rhoA=rhoA, rhoB=rhoB, nuA=1.0, nuB=0.1, mobility=0.1, beta=beta, kappa=kappa, gy=gy,
+                   rho_ref=rho_ref, cfl=0.5)
+    return mesh, prm, I.drop_field(mesh, radius, centre, 4.0)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("bubble", [False, True])
+def test_density_ratio_limit_of_the_printed_scheme(bubble):
+    """Eq. (oderrho) makes rho linear in phi, so at rhoB/rhoA = 1000 an overshoot
+    of phi past phiA by 0.1% (the diffuse interface overshoots by about that in
+    its first steps) gives rho <= 0, and the scheme as printed breaks down within
+    a few steps.  At a ratio of 20 the same drop and bubble stay finite, with rho
+    positive everywhere.  This is why the batched ensemble draws its density
+    ratio from [2, 20] instead of [2, 1000]."""
+    mesh, prm, phi0 = _ensemble_like(1000.0, bubble)
+    o = oracle.Oracle(mesh, prm).init(phi0)
+    for k in range(1, 21):
+        o.step(1, check=False)
+        m = o.moments()
+        if not np.all(np.isfinite(m["rho"])) or m["rho"].min() <= 0:
+            break
+    else:
+        pytest.fail("expected rho <= 0 within 20 steps at a density ratio of 1000")
+    assert k <= 10 and np.nanmax(m["phi"]) > 1.0 + 1.0 / 1000.0 - 1e-12
+    mesh, prm, phi0 = _ensemble_like(20.0, bubble)
+    o = oracle.Oracle(mesh, prm).init(phi0)
+    o.step(1000)
+    m = o.moments()
+    assert np.all(np.isfinite(m["phi"])) and m["rho"].min() > 0.5 * prm.rhoA
