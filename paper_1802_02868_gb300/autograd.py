@@ -41,16 +41,19 @@ class DugksLoss(torch.autograd.Function):
             r = sim.adjoint(problem.steps, problem.phi_target, ckpt_every=problem.ckpt_every)
         finally:
             sim.close()
+        # each gradient lives on the device (and in the dtype) of its own input
         ctx.save_for_backward(torch.as_tensor(r["dphi0"], dtype=phi0.dtype, device=phi0.device),
-                              torch.tensor(r["dkappa"], dtype=torch.float64),
-                              torch.tensor(r["dlambda"], dtype=torch.float64))
+                              torch.tensor(r["dkappa"], dtype=torch.float64, device=kappa.device),
+                              torch.tensor(r["dlambda"], dtype=torch.float64, device=mobility.device))
+        ctx.dtypes = (kappa.dtype, mobility.dtype)
         return torch.tensor(r["loss"], dtype=torch.float64, device=phi0.device)
 
     @staticmethod
     def backward(ctx, grad):
         dphi0, dk, dl = ctx.saved_tensors
         g = grad.to(torch.float64)
-        return (g.to(dphi0.device) * dphi0, (g.cpu() * dk).to(grad.device), (g.cpu() * dl).to(grad.device), None)
+        return (g.to(dphi0.device) * dphi0, (g.to(dk.device) * dk).to(ctx.dtypes[0]),
+                (g.to(dl.device) * dl).to(ctx.dtypes[1]), None)
 
 
 def interface_field(amplitudes, mesh, y0, wavelength, width, phiA=1.0, phiB=0.0):

@@ -60,3 +60,23 @@ def test_gradients_through_autograd_match_finite_differences(nx, ny, steps):
         km[name] = base - h
         fd = (_loss(prob, amps, **kp) - _loss(prob, amps, **km)) / (2 * h)
         assert float(t.grad) == pytest.approx(fd, rel=2e-5)
+
+
+def test_gradients_land_on_the_devices_of_their_inputs():
+    """phi0 built on the GPU, kappa and the mobility on the CPU: each gradient
+    arrives on its own input's device and equals the all-CPU result."""
+    c, amps, prob = _problem(16, 48, 10, seed=3)
+    grads = {}
+    for dev_phi, dev_par in (("cpu", "cpu"), ("cuda", "cpu"), ("cpu", "cuda")):
+        a = torch.tensor(amps, dtype=torch.float64, device=dev_phi, requires_grad=True)
+        kap = torch.tensor(c.params.kappa, dtype=torch.float64, device=dev_par, requires_grad=True)
+        mob = torch.tensor(c.params.mobility, dtype=torch.float64, device=dev_par, requires_grad=True)
+        L = DugksLoss.apply(interface_field(a, c.mesh, 24.0, 16.0, 4.0), kap, mob, prob)
+        L.backward()
+        assert a.grad.device.type == dev_phi
+        assert kap.grad.device.type == dev_par and mob.grad.device.type == dev_par
+        grads[(dev_phi, dev_par)] = [t.grad.cpu().numpy() for t in (a, kap, mob)]
+    ref = grads[("cpu", "cpu")]
+    for k, g in grads.items():
+        for x, y in zip(g, ref):
+            np.testing.assert_allclose(x, y, rtol=1e-12, atol=0)
