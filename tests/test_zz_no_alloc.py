@@ -8,7 +8,9 @@ tests check its sums against the existing dugks_conservation entry point on
 two calls in a row, the second on a smaller mesh so that scratch left by the
 first call cannot leak into it, and check that oversized meshes are refused.
 
-This file is collected last on purpose.
+The file name sorts last, so pytest collects it after every other test file:
+a run that stops at the first failure (-x) has then run every other test
+before this one, whose scratch array is shared process-wide.
 """
 import numpy as np
 import pytest
@@ -70,3 +72,26 @@ def test_static_conservation_refuses_oversized_mesh():
                                    buf.data_ptr(), 0)
     assert rc == -1
     assert torch.all(buf == 0)
+
+
+def _host_sums(phi, dx, dy, prm):
+    vol = dy[:, None] * dx[None, :]
+    drho = (prm.rhoA - prm.rhoB) / (prm.phiA - prm.phiB)
+    return np.sum(vol * phi), np.sum(vol * (prm.rhoB + drho * (phi - prm.phiB)))
+
+
+@pytest.mark.parametrize("nx,ny", [(1100, 1000), (4096, 4096)])
+def test_static_conservation_on_many_blocks_and_at_the_cap(nx, ny):
+    """1.1e6 cells (269 partial pairs, so the final reduction strides over more
+    partials than it has threads) and exactly DUGKS_STATIC_MAX_CELLS cells, each
+    against an FP64 sum on the host."""
+    assert nx * ny <= dugks.STATIC_MAX_CELLS
+    rng = np.random.default_rng(nx)
+    prm = I.Params(rhoA=3.0, rhoB=1.0)
+    phi = rng.random((ny, nx))
+    dx, dy = 0.5 + rng.random(nx), 0.5 + rng.random(ny)
+    mesh = I.Mesh(dx, dy, I.PERIODIC, I.PERIODIC)
+    got = _static_sums(mesh, prm, phi)
+    want = _host_sums(phi, dx, dy, prm)
+    assert got[0] == pytest.approx(want[0], rel=1e-12)
+    assert got[1] == pytest.approx(want[1], rel=1e-12)
