@@ -192,14 +192,18 @@ int dugks_kernel_bytes_per_cell(const dugks_sim *sim, int k, double *bytes);
    2 = 32x12 on 384 threads, 3 = 32x8 on 352 threads with the face fluxes in
    their own shared memory (two blocks per SM).  Strips, one thread block of
    288 threads marching up 32 columns in blocks of 32x8 cells (two blocks per
-   SM): 4 = strips of 8 blocks, 5 = 16 blocks, 6 = 32 blocks.  Every shape
+   SM): 4 = strips of 8 blocks, 5 = 16 blocks, 6 = 32 blocks.  Ring strips,
+   the same strips with every shared-memory region a ring of rows (nothing is
+   shifted between blocks) and the work of consecutive blocks merged into
+   three phases per block: 7 = strips of 8 blocks, 8 = 16 blocks, 9 = 32
+   blocks.  Every shape
    computes the same scheme: on uniform periodic meshes the results agree bit
    for bit, elsewhere to rounding.  dugks_autotune times every shape on the sim's current state for
    `steps` steps each (CUDA events on the sim's stream), restores the state and
    the per-instance status after each trial, keeps the fastest shape and
    returns its index and time per step.  It allocates a temporary snapshot of
    the state (cudaMalloc) for the duration of the call and synchronises. */
-#define DUGKS_NUM_TILE_SHAPES 7
+#define DUGKS_NUM_TILE_SHAPES 10
 int dugks_autotune(dugks_sim *sim, int steps, int *chosen, double *ms_per_step);
 int dugks_set_tile_shape(dugks_sim *sim, int shape);
 int dugks_tile_shape(const dugks_sim *sim, int *shape, int *bx, int *by);
@@ -276,7 +280,10 @@ int dugks_measure_alu_peaks(int iters_f32, int iters_f64, double *fp32_tflops, d
    with more than DUGKS_STATIC_MAX_CELLS cells are rejected with DUGKS_ERR_ARG
    before any device work.  The first call on a device looks up the scratch
    array's device address (cudaGetSymbolAddress, with that device current);
-   make that first call before any stream capture.  Every call overwrites the
+   make that first call before any stream capture.  The address is kept for
+   the life of the process: after a cudaDeviceReset (which unloads this
+   library's device code from that device) it is stale, so do not call this
+   entry point on a device that was reset since its first call.  Every call overwrites the
    scratch slots it uses, so no state carries over, but all calls share the one
    array: calls whose kernels overlap on the GPU (different streams, or
    different host threads) race and must be serialised by the caller. */

@@ -143,6 +143,8 @@ struct Tile {
     __device__ __forceinline__ int om(int axis, int pos) const { return UNI ? -1 : (gf[ge(axis, pos)] & 1) ? -1 : 0; }
     __device__ __forceinline__ int op(int axis, int pos) const { return UNI ? 1 : (gf[ge(axis, pos)] & 2) ? 1 : 0; }
     __device__ __forceinline__ T c(int k, int axis, int pos) const { return ga[k * L::NG + ge(axis, UNI ? 0 : pos)]; }
+    // index step from row y to row y + d of the R1 planes
+    __device__ __forceinline__ int rs1(int y, int d) const { return d * L::W1; }
 };
 
 // Face macroscopic variables from the nine bar distributions of each kind at
@@ -227,12 +229,13 @@ __device__ __forceinline__ void tile_face(const InstDev &I, const TL &S, int xa,
     const T h = Pr.h;
     const T area = S.c(10, 1 - A, pt);
     const T te1m = S.c(4, 1 - A, pt), te10 = S.c(5, 1 - A, pt), te1p = S.c(6, 1 - A, pt);
-    const int tstep = A == 0 ? TL::L::W1 : 1;
-    const int tm = S.om(1 - A, pt) * tstep, tp = S.op(1 - A, pt) * tstep;
+    // tangential neighbours: a row step for x faces, a column step for y faces
+    const int tm = A == 0 ? S.rs1(pt, S.om(1, pt)) : S.om(0, pt);
+    const int tp = A == 0 ? S.rs1(pt, S.op(1, pt)) : S.op(0, pt);
     T fb[Q], gb[Q];
     FaceAux<T> ax;
     if (UNI || (va && vb)) {
-        const int ia = TL::i1(xa, ya), ib = TL::i1(xb, yb);
+        const int ia = S.i1(xa, ya), ib = S.i1(xb, yb);
         const T wL = S.c(7, A, pa), wR = S.c(8, A, pa), invd = S.c(9, A, pa);
 #pragma unroll
         for (int q = 0; q < Q; q++) {
@@ -253,7 +256,7 @@ __device__ __forceinline__ void tile_face(const InstDev &I, const TL &S, int xa,
             fb[q] = v.x;
             gb[q] = v.y;
         }
-        const int ma = TL::i3(xa, ya), mb = TL::i3(xb, yb);
+        const int ma = S.i3(xa, ya), mb = S.i3(xb, yb);
         ax.mu = wL * S.mu[ma] + wR * S.mu[mb];
         ax.lapmu = wL * S.lmu[ia] + wR * S.lmu[ib];
         ax.gmux = wL * S.gmx[ia] + wR * S.gmx[ib];
@@ -266,14 +269,14 @@ __device__ __forceinline__ void tile_face(const InstDev &I, const TL &S, int xa,
         return;
     }
     int side, xc, yc, pc;
-    if (!va && vb && (S.gf[TL::ge(A, pb)] & 4)) { side = -1; xc = xb; yc = yb; pc = pb; }
-    else if (va && !vb && (S.gf[TL::ge(A, pa)] & 8)) { side = +1; xc = xa; yc = ya; pc = pa; }
+    if (!va && vb && (S.gf[S.ge(A, pb)] & 4)) { side = -1; xc = xb; yc = yb; pc = pb; }
+    else if (va && !vb && (S.gf[S.ge(A, pa)] & 8)) { side = +1; xc = xa; yc = ya; pc = pa; }
     else return;
     // wall face of cell c: Taylor reconstruction from the cell centre for the
     // outgoing and parallel directions, bounce-back for the incoming ones
-    const int ic = TL::i1(xc, yc);
-    const int nstep = A == 0 ? 1 : TL::L::W1;
-    const int nm = S.om(A, pc) * nstep, np = S.op(A, pc) * nstep;
+    const int ic = S.i1(xc, yc);
+    const int nm = A == 0 ? S.om(0, pc) : S.rs1(yc, S.om(1, pc));
+    const int np = A == 0 ? S.op(0, pc) : S.rs1(yc, S.op(1, pc));
     const T ne1m = S.c(4, A, pc), ne10 = S.c(5, A, pc), ne1p = S.c(6, A, pc);
     const T half_d = T(0.5) * S.c(10, A, pc);
 #pragma unroll
@@ -296,7 +299,7 @@ __device__ __forceinline__ void tile_face(const InstDev &I, const TL &S, int xa,
             gb[q] = gb[opp(q)];
         }
     }
-    ax.mu = S.mu[TL::i3(xc, yc)];
+    ax.mu = S.mu[S.i3(xc, yc)];
     ax.lapmu = S.lmu[ic];
     ax.gmux = A == 0 ? T(0) : S.gmx[ic];
     ax.gmuy = A == 1 ? T(0) : S.gmy[ic];

@@ -140,3 +140,34 @@ def test_viscosity_ratio_sweep_keeps_the_two_layer_profiles(prec):
     assert all(a < b for a, b in zip(errs, errs[1:]))
     assert s.status() == [0] * len(cases)
     s.close()
+
+
+@pytest.mark.parametrize("prec", [dugks.FP64, dugks.FP32])
+def test_cfl_sweep_instances_match_oracle_runs_of_their_own_counts(prec):
+    """Sec. 3.1's CFL sweep as one batch: dugks_batch_step_each brings the
+    instances at CFL 0.2, 0.4 and 0.8 to the same time t = 40 (283, 141 and 71
+    steps), and each instance matches an oracle run of its own step count:
+    in FP64 the distributions element by element to 1e-10 normwise, in FP32
+    phi to 1e-5 (L-infinity) and u to 1e-4 (L2-relative)."""
+    import oracle
+    cases = I.cfl_sweep(cfls=(0.2, 0.4, 0.8), n=64, radius=16.0)
+    b = dugks.Sim([c.mesh for c in cases], [c.params for c in cases], prec).init([c.phi0 for c in cases])
+    counts = [int(round(40.0 / b.dt(k))) for k in range(len(cases))]
+    assert counts == [283, 141, 71]
+    b.step_each(counts)
+    fb, gb = b.state()
+    mb = b.moments()
+    sl = _slices(cases)
+    for k, (c, n) in enumerate(zip(cases, counts)):
+        o = oracle.Oracle(c.mesh, c.params).init(c.phi0)
+        o.step(n)
+        if prec == dugks.FP64:
+            fo, go = o.state()
+            for got, ref in ((fb[:, sl[k]], fo.reshape(9, -1)), (gb[:, sl[k]], go.reshape(9, -1))):
+                assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < 1e-10, (k, n)
+        else:
+            mo = o.moments()
+            u, uo = np.stack([mb["ux"][k], mb["uy"][k]]), np.stack([mo["ux"], mo["uy"]])
+            assert np.max(np.abs(mb["phi"][k] - mo["phi"])) < 1e-5, (k, n)
+            assert np.linalg.norm(u - uo) / np.linalg.norm(uo) < 1e-4, (k, n)
+    b.close()
