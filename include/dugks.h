@@ -192,18 +192,14 @@ int dugks_kernel_bytes_per_cell(const dugks_sim *sim, int k, double *bytes);
    2 = 32x12 on 384 threads, 3 = 32x8 on 352 threads with the face fluxes in
    their own shared memory (two blocks per SM).  Strips, one thread block of
    288 threads marching up 32 columns in blocks of 32x8 cells (two blocks per
-   SM): 4 = strips of 8 blocks, 5 = 16 blocks, 6 = 32 blocks.  Ring strips,
-   the same strips with every shared-memory region a ring of rows (nothing is
-   shifted between blocks) and the work of consecutive blocks merged into
-   three phases per block: 7 = strips of 8 blocks, 8 = 16 blocks, 9 = 32
-   blocks.  Every shape
+   SM): 4 = strips of 8 blocks, 5 = 16 blocks, 6 = 32 blocks.  Every shape
    computes the same scheme: on uniform periodic meshes the results agree bit
    for bit, elsewhere to rounding.  dugks_autotune times every shape on the sim's current state for
    `steps` steps each (CUDA events on the sim's stream), restores the state and
    the per-instance status after each trial, keeps the fastest shape and
    returns its index and time per step.  It allocates a temporary snapshot of
    the state (cudaMalloc) for the duration of the call and synchronises. */
-#define DUGKS_NUM_TILE_SHAPES 10
+#define DUGKS_NUM_TILE_SHAPES 7
 int dugks_autotune(dugks_sim *sim, int steps, int *chosen, double *ms_per_step);
 int dugks_set_tile_shape(dugks_sim *sim, int shape);
 int dugks_tile_shape(const dugks_sim *sim, int *shape, int *bx, int *by);

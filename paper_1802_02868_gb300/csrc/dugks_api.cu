@@ -16,7 +16,7 @@
 #include "dugks_common.cuh"
 #include "dugks_kernels.cuh"
 #include "dugks_fused.cuh"
-#include "dugks_ring.cuh"
+#include "dugks_strip.cuh"
 #include "dugks_adjoint.cuh"
 #include "dugks_diag.cuh"
 
@@ -93,9 +93,8 @@ namespace {
 // tile per thread block of NT threads; "sep" gives the face fluxes their own
 // shared memory (two blocks per SM instead of three in FP32).
 struct ShapeDesc {
-    int bx, by, nt, sep, nb;   // nb > 0: a strip of up to nb blocks per thread block (k_strip or k_ring)
+    int bx, by, nt, sep, nb;   // nb > 0: a strip of up to nb blocks per thread block (k_strip)
     const char *name;
-    int ring;                  // 1: k_ring (ring-buffered rows, merged phases)
 };
 const ShapeDesc kShapes[DUGKS_NUM_TILE_SHAPES] = {{32, 8, 256, 0, 0, "32x8"},
                                                   {32, 4, 128, 0, 0, "32x4/128"},
@@ -103,10 +102,7 @@ const ShapeDesc kShapes[DUGKS_NUM_TILE_SHAPES] = {{32, 8, 256, 0, 0, "32x8"},
                                                   {32, 8, 352, 1, 0, "32x8/352 sep"},
                                                   {32, 8, 288, 0, 8, "32x8 strip8/288"},
                                                   {32, 8, 288, 0, 16, "32x8 strip16/288"},
-                                                  {32, 8, 288, 0, 32, "32x8 strip32/288"},
-                                                  {32, 8, 288, 0, 8, "32x8 ring8/288", 1},
-                                                  {32, 8, 288, 0, 16, "32x8 ring16/288", 1},
-                                                  {32, 8, 288, 0, 32, "32x8 ring32/288", 1}};
+                                                  {32, 8, 288, 0, 32, "32x8 strip32/288"}};
 
 const char *kNames[K_COUNT] = {"k_mu", "k_macro", "k_cell", "k_face", "k_init", "k_reduce", "k_step", "k_diag"};
 
@@ -309,24 +305,6 @@ int prepare_strip()
     return DUGKS_OK;
 }
 
-template <typename T, int BX, int BY, int NT>
-int prepare_ring()
-{
-    using RL = RingLayout<T, BX, BY>;
-    constexpr int MB = fused_minb<T, NT, false>();
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_ring<T, BX, BY, NT, MB, false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RL::bytes);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_ring<T, BX, BY, NT, MB, true>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RL::bytes);
-        if (e != cudaSuccess) return cuda_status(e);
-        attr_set = true;
-    }
-    return DUGKS_OK;
-}
-
 // fused-step tile table of shape k: the uniform periodic instances' tiles first
 int ensure_tiles(dugks_sim *s, int k)
 {
@@ -368,9 +346,6 @@ int prepare_fused(dugks_sim *s)
     case 4:
     case 5:
     case 6: return prepare_strip<T, 32, 8, 288>();
-    case 7:
-    case 8:
-    case 9: return prepare_ring<T, 32, 8, 288>();
     default: return prepare_shape<T, 32, 8, 256, false>();
     }
 }
@@ -407,17 +382,6 @@ void enqueue_strip(dugks_sim *s, int k, const StepIO<T> &io, cudaStream_t st)
     if (ng > 0) k_strip<T, BX, BY, NT, MB, false><<<(unsigned)ng, NT, SL::bytes, st>>>(s->d_inst, s->d_tiles_s[k] + nu, geo, io);
 }
 
-template <typename T, int BX, int BY, int NT>
-void enqueue_ring(dugks_sim *s, int k, const StepIO<T> &io, cudaStream_t st)
-{
-    using RL = RingLayout<T, BX, BY>;
-    constexpr int MB = fused_minb<T, NT, false>();
-    const int nu = s->n_uni_s[k], ng = s->n_tiles_s[k] - nu;
-    const AxisRecT<T> *geo = (const AxisRecT<T> *)s->d_geoT;
-    if (nu > 0) k_ring<T, BX, BY, NT, MB, true><<<(unsigned)nu, NT, RL::bytes, st>>>(s->d_inst, s->d_tiles_s[k], geo, io);
-    if (ng > 0) k_ring<T, BX, BY, NT, MB, false><<<(unsigned)ng, NT, RL::bytes, st>>>(s->d_inst, s->d_tiles_s[k] + nu, geo, io);
-}
-
 template <typename T, int BX, int BY, int NT, bool SEP>
 void enqueue_shape(dugks_sim *s, int k, const StepIO<T> &io, cudaStream_t st)
 {
@@ -439,9 +403,6 @@ void enqueue_fused(dugks_sim *s, const StepIO<T> &io, cudaStream_t st)
     case 4:
     case 5:
     case 6: enqueue_strip<T, 32, 8, 288>(s, s->shape, io, st); break;
-    case 7:
-    case 8:
-    case 9: enqueue_ring<T, 32, 8, 288>(s, s->shape, io, st); break;
     default: enqueue_shape<T, 32, 8, 256, false>(s, 0, io, st); break;
     }
 }

@@ -438,7 +438,7 @@ def measure_alu_peaks(iters_f32=262144, iters_f64=4096, stream=0):
     return {"fp32": a.value, "fp32x2": b.value, "fp64": c.value}
 
 
-NUM_TILE_SHAPES = 10
+NUM_TILE_SHAPES = 7
 
 
 def tile_shape_name(k):

@@ -9,7 +9,7 @@ is met):
   (the u target is missed by 8%); FP64 6e-14.
 - Ensemble: its 512x512 instance and a tanh-stretched 96x288 channel with
   walls (three strips of up to 16 blocks), 1000 steps through the fused
-  16-block strip and ring strip: phi <= 7e-8, u 4.2e-5.
+  16-block strip: phi <= 7e-8, u 4.2e-5.
 - Adjoint, Rayleigh-Taylor 256x512, 4000 steps, checkpoint every 100: the FP32
   gradient against the FP64 one, dL/dphi0 8.5e-5 (L2-relative), dL/dkappa
   8.1e-5, dL/dlambda 2.0e-5, the loss 2.3e-5.
@@ -54,7 +54,7 @@ def test_rayleigh_taylor_fp32_against_oracle_after_1000_steps():
             assert phi_err < 1e-12 and u_err < 1e-12, (phi_err, u_err)
 
 
-@pytest.mark.parametrize("shape", [5, 8])
+@pytest.mark.parametrize("shape", [5])
 def test_ensemble_fp32_large_and_walled_instances_against_oracle(shape):
     ens = I.batched_ensemble(512)
     big = next(c for c in ens if c.mesh.nx == 512)

@@ -194,10 +194,9 @@ def test_graph_replay_matches_plain_launches(monkeypatch):
 @pytest.mark.parametrize("prec", [dugks.FP64, dugks.FP32])
 def test_every_shape_is_bit_identical_on_uniform_periodic_meshes(prec):
     """On uniform periodic meshes the strips (which prefetch the next block's
-    rows and refill the shifted rings), the ring strips (which merge the phases
-    of consecutive blocks) and every tile shape execute the same arithmetic per
-    cell: after 20 steps of a batch of uneven sizes, every shape holds the same
-    bits."""
+    rows and refill the shifted rings) and every tile shape execute the same
+    arithmetic per cell: after 20 steps of a batch of uneven sizes, every shape
+    holds the same bits."""
     cases = [I.stationary_drop(n=96, radius=24.0), I.stationary_drop(n=160, radius=40.0), I.roofline_drop(64)]
     ref = None
     for k in range(dugks.NUM_TILE_SHAPES):

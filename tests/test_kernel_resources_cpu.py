@@ -3,10 +3,10 @@ CPU (nvcc cross-compiles for sm_103a; nothing runs on a GPU).
 
 The step's speed rests on how many thread blocks an SM holds and on the
 kernels not spilling registers:
-- the FP32 strip and ring strip (288 threads) are launched for 2 blocks per
-  SM, so their shared memory must leave room for two;
+- the FP32 strip (288 threads) is launched for 2 blocks per SM, so its shared
+  memory must leave room for two;
 - the FP32 32x8 tile (256 threads) for 3 blocks per SM;
-- the FP64 strip, ring strip and tile for 1.
+- the FP64 strip and tile for 1.
 A GB300 SM has 228 KB of shared memory, up to 227 KB per block, and reserves
 1 KB per resident block.  The FP32 strip must also compile without spilling.
 """
@@ -42,18 +42,16 @@ def test_shared_memory_of_each_shape_fits_its_blocks_per_sm(tmp_path):
         '#include "%s"\n'
         "#include <cstdio>\n"
         "int main() {\n"
-        '  printf("%%zu %%zu %%zu %%zu %%zu %%zu\\n", dugks::StripLayout<float, 32, 8>::bytes,\n'
+        '  printf("%%zu %%zu %%zu %%zu\\n", dugks::StripLayout<float, 32, 8>::bytes,\n'
         "         dugks::StripLayout<double, 32, 8>::bytes, dugks::FusedLayout<float, 32, 8, false>::bytes,\n"
-        "         dugks::FusedLayout<double, 32, 8, false>::bytes, dugks::RingLayout<float, 32, 8>::bytes,\n"
-        "         dugks::RingLayout<double, 32, 8>::bytes);\n"
-        "}\n" % os.path.join(CSRC, "dugks_ring.cuh"))
+        "         dugks::FusedLayout<double, 32, 8, false>::bytes);\n"
+        "}\n" % os.path.join(CSRC, "dugks_strip.cuh"))
     exe = tmp_path / "sizes"
     r = subprocess.run([_nvcc(), str(src), "-o", str(exe)] + ARCH + FLAGS, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
-    strip32, strip64, tile32, tile64, ring32, ring64 = (int(v) for v in subprocess.run(
-        [str(exe)], capture_output=True, text=True).stdout.split())
+    strip32, strip64, tile32, tile64 = (int(v) for v in subprocess.run([str(exe)], capture_output=True,
+                                                                          text=True).stdout.split())
     assert _fits(strip32, 2), strip32
-    assert _fits(ring32, 2) and _fits(ring64, 1), (ring32, ring64)
     assert _fits(tile32, 3), tile32
     assert _fits(strip64, 1) and _fits(tile64, 1), (strip64, tile64)
 
@@ -64,14 +62,14 @@ def test_fp32_strips_compile_without_spills(tmp_path):
                         "-Xcompiler", "-fPIC"] + ARCH + FLAGS, capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
     lines = r.stderr.splitlines()
-    found = {"k_strip": 0, "k_ring": 0}
+    found = {"k_strip": 0}
     for i, line in enumerate(lines):
         m = re.search(r"Compiling entry function '(\S+)'", line)
-        # mangled k_strip<float, 32, 8, 288, ...> and k_ring<float, 32, 8, 288, ...>
+        # mangled k_strip<float, 32, 8, 288, ...>
         for name in found:
             if m and (name + "IfLi32ELi8ELi288E") in m.group(1):
                 found[name] += 1
                 props = " ".join(lines[i + 1:i + 4])
                 spill = re.search(r"(\d+) bytes spill stores", props)
                 assert spill is not None and int(spill.group(1)) == 0, (m.group(1), props)
-    assert found == {"k_strip": 2, "k_ring": 2}, "expected the general and the uniform FP32 kernels: %s" % found
+    assert found == {"k_strip": 2}, "expected the general and the uniform FP32 strip: %s" % found
