@@ -8,7 +8,7 @@
 //   k_cell  grad p, equilibria, sources, bar-plus (Eq. relations1)
 //   k_face  reconstruction, face macros, originals, flux, update (Eq. updatef)
 // Reverse, given the adjoint xb of the state at n+1:
-//   ka_face   update and faces  -> adjoint of bar-plus and of the face aux fields
+//   ka_face_t update and faces  -> adjoint of bar-plus and of the face aux fields
 //   ka_cell   bar-plus          -> adjoint of tilde, of u, p, phi, mu and gradients
 //   ka_macro  transpose grad p, then p, u, F -> adjoint of tilde f, phi, grad mu, ...
 //   ka_mu     transpose grad mu, lap mu, then mu -> adjoint of phi, lap phi
@@ -269,58 +269,85 @@ __device__ __forceinline__ void block_add_param(double *dst, T v)
 }
 
 // ---------------------------------------------------------------------------
-// faces
+// faces: the transposes of the interior and wall faces (Eqs. fbar_h,
+// conservedVariable with h, original-function, microfluxf) for a TX x TY tile
+// per thread block.  Bar-plus, the face aux fields and the incoming adjoints
+// of the tile and its one-cell ring are staged in shared memory with
+// coalesced loads, the scatter of the face transposes goes into shared
+// accumulators, and each accumulator slot is added to global memory once.
+// Each cell owns its west and south faces, and the wall faces at the high end.
 // ---------------------------------------------------------------------------
+template <typename T>
+struct AdjTile {
+    static constexpr int W = TX + 2, H = TY + 2, A = W * H;   // region: columns -1..TX, rows -1..TY
+    static constexpr int NG = W + H;                          // geometry entries: columns, then rows
+    static constexpr int BP = 0, AUX = 2 * Q, XF = 2 * Q + 8, XG = 3 * Q + 8;
+    static constexpr int NIN = 4 * Q + 8;                     // staged planes
+    static constexpr int NACC = 2 * Q + 8;                    // accumulators: bar-plus, then aux adjoints
+    static constexpr size_t al(size_t v) { return (v + 15) / 16 * 16; }
+    static constexpr size_t o_in = al((sizeof(T) * 7 + sizeof(int) * 2) * NG);
+    static constexpr size_t o_acc = al(o_in + sizeof(T) * NIN * A);
+    static constexpr size_t bytes = al(o_acc + sizeof(T) * NACC * A);
+    static __device__ __forceinline__ int ri(int x, int y) { return (y + 1) * W + (x + 1); }
+    static __device__ __forceinline__ int ex(int x) { return x + 1; }
+    static __device__ __forceinline__ int ey(int y) { return W + y + 1; }
+};
+
+template <typename T>
+struct AdjTileView {
+    using AT = AdjTile<T>;
+    const T *ga;     // [7][NG]: d, e1m, e10, e1p, wL, wR, invd
+    const int *gf;   // [NG] flags: 1 low neighbour, 2 high neighbour, 4 low wall, 8 high wall
+    const T *in;     // [NIN][A]
+    T *acc;          // [NACC][A]
+    __device__ __forceinline__ T g(int k, int e) const { return ga[k * AT::NG + e]; }
+    __device__ __forceinline__ T v(int plane, int r) const { return in[plane * AT::A + r]; }
+    __device__ __forceinline__ void add(int plane, int r, T val) const { atomicAdd(acc + plane * AT::A + r, val); }
+};
+
 template <typename T, int A>
-__device__ void interior_face_adj(const InstDev &I, const ParT<T> &Pr, const Planes<T> &P, const AdjPlanes<T> &Ad,
-                                  const AxisRec *__restrict__ geo, int iL, int jL, int iR, int jR, T &lamb)
+__device__ void interior_face_adj_t(const ParT<T> &Pr, const AdjTileView<T> &V, int xL, int yL, int xR, int yR, T &lamb)
 {
-    const long long N = P.N;
-    const AxisRec &rn = (A == 0) ? geo[I.gx_off + iL] : geo[I.gy_off + jL];
-    const AxisRec &rt = (A == 0) ? geo[I.gy_off + jL] : geo[I.gx_off + iL];
-    const T wL = T(rn.wL), wR = T(rn.wR), invd = T(rn.invd);
-    const T em = T(rt.e1m), e0 = T(rt.e10), ep = T(rt.e1p);
-    const T area = T(rt.d);
-    const long long cL = cell_of(I, iL, jL), cR = cell_of(I, iR, jR);
-    long long cLm, cLp, cRm, cRp;
-    if (A == 0) {
-        cLm = cell_of(I, iL, rt.km); cLp = cell_of(I, iL, rt.kp);
-        cRm = cell_of(I, iR, rt.km); cRp = cell_of(I, iR, rt.kp);
-    } else {
-        cLm = cell_of(I, rt.km, jL); cLp = cell_of(I, rt.kp, jL);
-        cRm = cell_of(I, rt.km, jR); cRp = cell_of(I, rt.kp, jR);
-    }
+    using AT = AdjTile<T>;
+    const int rL = AT::ri(xL, yL), rR = AT::ri(xR, yR);
+    const int en = A == 0 ? AT::ex(xL) : AT::ey(yL);     // normal axis: the high face of L
+    const int et = A == 0 ? AT::ey(yL) : AT::ex(xL);     // tangential axis
+    const T wL = V.g(4, en), wR = V.g(5, en), invd = V.g(6, en);
+    const T em = V.g(1, et), e0 = V.g(2, et), ep = V.g(3, et);
+    const T area = V.g(0, et);
+    const int ft = V.gf[et], tstep = A == 0 ? AT::W : 1;
+    const int tm = (ft & 1) ? -tstep : 0, tp = (ft & 2) ? tstep : 0;   // a wall ghost is the cell itself
     const T h = Pr.h;
     T fb[Q], gb[Q];
 #pragma unroll
     for (int q = 0; q < Q; q++) {
 #pragma unroll
         for (int kind = 0; kind < 2; kind++) {
-            const T *B = (kind == 0 ? P.fbp : P.gbp) + q * N;
-            const T bL = B[cL], bR = B[cR];
-            const T tL = em * B[cLm] + e0 * bL + ep * B[cLp];
-            const T tR = em * B[cRm] + e0 * bR + ep * B[cRp];
+            const int pl = AT::BP + kind * Q + q;
+            const T bL = V.v(pl, rL), bR = V.v(pl, rR);
+            const T tL = em * V.v(pl, rL + tm) + e0 * bL + ep * V.v(pl, rL + tp);
+            const T tR = em * V.v(pl, rR + tm) + e0 * bR + ep * V.v(pl, rR + tp);
             (kind == 0 ? fb : gb)[q] = (wL * bL + wR * bR) - h * (T(ca(q, A)) * ((bR - bL) * invd) + T(ca(q, 1 - A)) * (wL * tL + wR * tR));
         }
     }
     FaceAux<T> ax;
-    ax.mu = wL * P.mu[cL] + wR * P.mu[cR];
-    ax.lapmu = wL * P.lapmu[cL] + wR * P.lapmu[cR];
-    ax.gmux = wL * P.gmux[cL] + wR * P.gmux[cR];
-    ax.gmuy = wL * P.gmuy[cL] + wR * P.gmuy[cR];
-    ax.gpx = wL * P.gpx[cL] + wR * P.gpx[cR];
-    ax.gpy = wL * P.gpy[cL] + wR * P.gpy[cR];
-    ax.gphix = wL * P.gphix[cL] + wR * P.gphix[cR];
-    ax.gphiy = wL * P.gphiy[cL] + wR * P.gphiy[cR];
+    ax.mu = wL * V.v(AT::AUX + 0, rL) + wR * V.v(AT::AUX + 0, rR);
+    ax.lapmu = wL * V.v(AT::AUX + 1, rL) + wR * V.v(AT::AUX + 1, rR);
+    ax.gmux = wL * V.v(AT::AUX + 2, rL) + wR * V.v(AT::AUX + 2, rR);
+    ax.gmuy = wL * V.v(AT::AUX + 3, rL) + wR * V.v(AT::AUX + 3, rR);
+    ax.gpx = wL * V.v(AT::AUX + 4, rL) + wR * V.v(AT::AUX + 4, rR);
+    ax.gpy = wL * V.v(AT::AUX + 5, rL) + wR * V.v(AT::AUX + 5, rR);
+    ax.gphix = wL * V.v(AT::AUX + 6, rL) + wR * V.v(AT::AUX + 6, rR);
+    ax.gphiy = wL * V.v(AT::AUX + 7, rL) + wR * V.v(AT::AUX + 7, rR);
     // the flux value enters J_L with + and J_R with -; J-bar = -dt/|V| x-bar
-    const T dtvL = Pr.dt / (T(geo[I.gx_off + iL].d) * T(geo[I.gy_off + jL].d));
-    const T dtvR = Pr.dt / (T(geo[I.gx_off + iR].d) * T(geo[I.gy_off + jR].d));
+    const T dtvL = Pr.dt / (V.g(0, AT::ex(xL)) * V.g(0, AT::ey(yL)));
+    const T dtvR = Pr.dt / (V.g(0, AT::ex(xR)) * V.g(0, AT::ey(yR)));
     T Ffb[6], Fgb[6];
 #pragma unroll
     for (int k = 0; k < 6; k++) {
         const int q = fset<A>(k);
-        Ffb[k] = dtvR * Ad.xf[q * N + cR] - dtvL * Ad.xf[q * N + cL];
-        Fgb[k] = dtvR * Ad.xg[q * N + cR] - dtvL * Ad.xg[q * N + cL];
+        Ffb[k] = dtvR * V.v(AT::XF + q, rR) - dtvL * V.v(AT::XF + q, rL);
+        Fgb[k] = dtvR * V.v(AT::XG + q, rR) - dtvL * V.v(AT::XG + q, rL);
     }
     T fbb[Q], gbb[Q];
     FaceAux<T> axb;
@@ -330,50 +357,43 @@ __device__ void interior_face_adj(const InstDev &I, const ParT<T> &Pr, const Pla
 #pragma unroll
         for (int kind = 0; kind < 2; kind++) {
             const T bb = (kind == 0 ? fbb : gbb)[q];
-            T *B = Ad.bp + (kind * Q + q) * N;
+            const int pl = kind * Q + q;
             const T k1 = h * T(ca(q, A)) * invd;
-            atomicAdd(B + cL, (wL + k1) * bb);
-            atomicAdd(B + cR, (wR - k1) * bb);
+            V.add(pl, rL, (wL + k1) * bb);
+            V.add(pl, rR, (wR - k1) * bb);
             if (ca(q, 1 - A)) {
                 const T kt = -h * T(ca(q, 1 - A)) * bb;
-                atomicAdd(B + cLm, kt * wL * em);
-                atomicAdd(B + cL, kt * wL * e0);
-                atomicAdd(B + cLp, kt * wL * ep);
-                atomicAdd(B + cRm, kt * wR * em);
-                atomicAdd(B + cR, kt * wR * e0);
-                atomicAdd(B + cRp, kt * wR * ep);
+                V.add(pl, rL + tm, kt * wL * em);
+                V.add(pl, rL, kt * wL * e0);
+                V.add(pl, rL + tp, kt * wL * ep);
+                V.add(pl, rR + tm, kt * wR * em);
+                V.add(pl, rR, kt * wR * e0);
+                V.add(pl, rR + tp, kt * wR * ep);
             }
         }
     }
-    T *aux[8] = {Ad.mu, Ad.lapmu, Ad.gmx, Ad.gmy, Ad.gpx, Ad.gpy, Ad.gfx, Ad.gfy};
     const T vals[8] = {axb.mu, axb.lapmu, axb.gmux, axb.gmuy, axb.gpx, axb.gpy, axb.gphix, axb.gphiy};
 #pragma unroll
     for (int k = 0; k < 8; k++) {
-        atomicAdd(aux[k] + cL, wL * vals[k]);
-        atomicAdd(aux[k] + cR, wR * vals[k]);
+        V.add(2 * Q + k, rL, wL * vals[k]);
+        V.add(2 * Q + k, rR, wR * vals[k]);
     }
 }
 
 template <typename T, int A>
-__device__ void wall_face_adj(const InstDev &I, const ParT<T> &Pr, const Planes<T> &P, const AdjPlanes<T> &Ad,
-                              const AxisRec *__restrict__ geo, int i, int j, int side, T &lamb)
+__device__ void wall_face_adj_t(const ParT<T> &Pr, const AdjTileView<T> &V, int x, int y, int side, T &lamb)
 {
-    const long long N = P.N;
-    const AxisRec &rn = (A == 0) ? geo[I.gx_off + i] : geo[I.gy_off + j];
-    const AxisRec &rt = (A == 0) ? geo[I.gy_off + j] : geo[I.gx_off + i];
-    const long long c = cell_of(I, i, j);
-    long long cnm, cnp, ctm, ctp;
-    if (A == 0) {
-        cnm = cell_of(I, rn.km, j); cnp = cell_of(I, rn.kp, j);
-        ctm = cell_of(I, i, rt.km); ctp = cell_of(I, i, rt.kp);
-    } else {
-        cnm = cell_of(I, i, rn.km); cnp = cell_of(I, i, rn.kp);
-        ctm = cell_of(I, rt.km, j); ctp = cell_of(I, rt.kp, j);
-    }
-    const T h = Pr.h, half_d = T(0.5) * T(rn.d);
-    const T nm = T(rn.e1m), n0 = T(rn.e10), np = T(rn.e1p);
-    const T tm = T(rt.e1m), t0 = T(rt.e10), tp = T(rt.e1p);
-    const T area = T(rt.d);
+    using AT = AdjTile<T>;
+    const int r = AT::ri(x, y);
+    const int en = A == 0 ? AT::ex(x) : AT::ey(y), et = A == 0 ? AT::ey(y) : AT::ex(x);
+    const int fn = V.gf[en], ft = V.gf[et];
+    const int nstep = A == 0 ? 1 : AT::W, tstep = A == 0 ? AT::W : 1;
+    const int nmo = (fn & 1) ? -nstep : 0, npo = (fn & 2) ? nstep : 0;   // a wall ghost is the cell itself
+    const int tmo = (ft & 1) ? -tstep : 0, tpo = (ft & 2) ? tstep : 0;
+    const T h = Pr.h, half_d = T(0.5) * V.g(0, en);
+    const T nm = V.g(1, en), n0 = V.g(2, en), np = V.g(3, en);
+    const T tm = V.g(1, et), t0 = V.g(2, et), tp = V.g(3, et);
+    const T area = V.g(0, et);
     T fb[Q], gb[Q];
 #pragma unroll
     for (int q = 0; q < Q; q++) {
@@ -382,9 +402,10 @@ __device__ void wall_face_adj(const InstDev &I, const ParT<T> &Pr, const Planes<
         const T ht = h * T(ca(q, 1 - A));
 #pragma unroll
         for (int kind = 0; kind < 2; kind++) {
-            const T *B = (kind == 0 ? P.fbp : P.gbp) + q * N;
-            const T b = B[c];
-            (kind == 0 ? fb : gb)[q] = b + off * (nm * B[cnm] + n0 * b + np * B[cnp]) - ht * (tm * B[ctm] + t0 * b + tp * B[ctp]);
+            const int pl = AT::BP + kind * Q + q;
+            const T b = V.v(pl, r);
+            (kind == 0 ? fb : gb)[q] = b + off * (nm * V.v(pl, r + nmo) + n0 * b + np * V.v(pl, r + npo))
+                                     - ht * (tm * V.v(pl, r + tmo) + t0 * b + tp * V.v(pl, r + tpo));
         }
     }
 #pragma unroll
@@ -395,22 +416,22 @@ __device__ void wall_face_adj(const InstDev &I, const ParT<T> &Pr, const Planes<
         }
     }
     FaceAux<T> ax;
-    ax.mu = P.mu[c];
-    ax.lapmu = P.lapmu[c];
-    ax.gmux = (A == 0) ? T(0) : P.gmux[c];
-    ax.gmuy = (A == 1) ? T(0) : P.gmuy[c];
-    ax.gpx = (A == 0) ? T(0) : P.gpx[c];
-    ax.gpy = (A == 1) ? T(0) : P.gpy[c];
-    ax.gphix = (A == 0) ? T(0) : P.gphix[c];
-    ax.gphiy = (A == 1) ? T(0) : P.gphiy[c];
+    ax.mu = V.v(AT::AUX + 0, r);
+    ax.lapmu = V.v(AT::AUX + 1, r);
+    ax.gmux = (A == 0) ? T(0) : V.v(AT::AUX + 2, r);
+    ax.gmuy = (A == 1) ? T(0) : V.v(AT::AUX + 3, r);
+    ax.gpx = (A == 0) ? T(0) : V.v(AT::AUX + 4, r);
+    ax.gpy = (A == 1) ? T(0) : V.v(AT::AUX + 5, r);
+    ax.gphix = (A == 0) ? T(0) : V.v(AT::AUX + 6, r);
+    ax.gphiy = (A == 1) ? T(0) : V.v(AT::AUX + 7, r);
     // the flux value enters J_c with the sign of the side
-    const T dtv = Pr.dt / (T(geo[I.gx_off + i].d) * T(geo[I.gy_off + j].d));
+    const T dtv = Pr.dt / (V.g(0, AT::ex(x)) * V.g(0, AT::ey(y)));
     T Ffb[6], Fgb[6];
 #pragma unroll
     for (int k = 0; k < 6; k++) {
         const int q = fset<A>(k);
-        Ffb[k] = -T(side) * dtv * Ad.xf[q * N + c];
-        Fgb[k] = -T(side) * dtv * Ad.xg[q * N + c];
+        Ffb[k] = -T(side) * dtv * V.v(AT::XF + q, r);
+        Fgb[k] = -T(side) * dtv * V.v(AT::XG + q, r);
     }
     T fbb[Q], gbb[Q];
     FaceAux<T> axb;
@@ -431,50 +452,125 @@ __device__ void wall_face_adj(const InstDev &I, const ParT<T> &Pr, const Planes<
 #pragma unroll
         for (int kind = 0; kind < 2; kind++) {
             const T bb = (kind == 0 ? fbb : gbb)[q];
-            T *B = Ad.bp + (kind * Q + q) * N;
-            atomicAdd(B + c, (T(1) + off * n0 - ht * t0) * bb);
-            atomicAdd(B + cnm, off * nm * bb);
-            atomicAdd(B + cnp, off * np * bb);
-            atomicAdd(B + ctm, -ht * tm * bb);
-            atomicAdd(B + ctp, -ht * tp * bb);
+            const int pl = kind * Q + q;
+            V.add(pl, r, (T(1) + off * n0 - ht * t0) * bb);
+            V.add(pl, r + nmo, off * nm * bb);
+            V.add(pl, r + npo, off * np * bb);
+            V.add(pl, r + tmo, -ht * tm * bb);
+            V.add(pl, r + tpo, -ht * tp * bb);
         }
     }
-    atomicAdd(Ad.mu + c, axb.mu);
-    atomicAdd(Ad.lapmu + c, axb.lapmu);
-    if (A == 1) { atomicAdd(Ad.gmx + c, axb.gmux); atomicAdd(Ad.gpx + c, axb.gpx); atomicAdd(Ad.gfx + c, axb.gphix); }
-    if (A == 0) { atomicAdd(Ad.gmy + c, axb.gmuy); atomicAdd(Ad.gpy + c, axb.gpy); atomicAdd(Ad.gfy + c, axb.gphiy); }
+    V.add(2 * Q + 0, r, axb.mu);
+    V.add(2 * Q + 1, r, axb.lapmu);
+    if (A == 1) { V.add(2 * Q + 2, r, axb.gmux); V.add(2 * Q + 4, r, axb.gpx); V.add(2 * Q + 6, r, axb.gphix); }
+    if (A == 0) { V.add(2 * Q + 3, r, axb.gmuy); V.add(2 * Q + 5, r, axb.gpy); V.add(2 * Q + 7, r, axb.gphiy); }
 }
 
-// update and faces: x_new = 4/3 bar-plus - 1/3 x - dt/|V| J (Eqs. relations2, updatef).
-// Each cell owns its west and south faces (and the wall faces at the high end).
+// update and faces of a tile: x_new = 4/3 bar-plus - 1/3 x - dt/|V| J
+// (Eqs. relations2, updatef)
 template <typename T>
-__global__ void __launch_bounds__(TX *TY) ka_face(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles,
-                                                  const AxisRec *__restrict__ geo, Planes<T> P, AdjPlanes<T> Ad)
+__global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 2 : 1)
+    ka_face_t(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles, const AxisRecT<T> *__restrict__ geo,
+              Planes<T> P, AdjPlanes<T> Ad)
 {
+    using AT = AdjTile<T>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    T *ga = (T *)smem;
+    int *gg = (int *)(ga + 7 * AT::NG), *gf = gg + AT::NG;
+    T *in = (T *)(smem + AT::o_in);
+    T *acc = (T *)(smem + AT::o_acc);
     const int4 t = tiles[blockIdx.x];
     const InstDev &I = insts[t.x];
     const ParT<T> &Pr = par<T>(I);
-    const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
-    T lamb = 0;
-    if (i < I.nx && j < I.ny) {
-        const AxisRec &ax = geo[I.gx_off + i];
-        const AxisRec &ay = geo[I.gy_off + j];
-        const long long c = cell_of(I, i, j);
-        const long long N = P.N;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    const int i0 = t.y, j0 = t.z;
+    const long long N = P.N;
+    // geometry of the region's columns and rows (wrapped on a periodic axis,
+    // -1 outside the domain)
+    for (int e = tid; e < AT::NG; e += TX * TY) {
+        const bool isx = e < AT::W;
+        const int n = isx ? I.nx : I.ny;
+        int g = isx ? i0 + e - 1 : j0 + (e - AT::W) - 1;
+        if ((isx ? I.bcx : I.bcy) == 0) {
+            while (g < 0) g += n;
+            while (g >= n) g -= n;
+        } else if (g < 0 || g >= n) {
+            g = -1;
+        }
+        T v[7] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+        int fl = 0;
+        if (g >= 0) {
+            const AxisRecT<T> &R = geo[(isx ? I.gx_off : I.gy_off) + g];
+            v[0] = R.d; v[1] = R.e1m; v[2] = R.e10; v[3] = R.e1p; v[4] = R.wL; v[5] = R.wR; v[6] = R.invd;
+            fl = (R.km == g ? 0 : 1) | (R.kp == g ? 0 : 2) | (R.lo_wall ? 4 : 0) | (R.hi_wall ? 8 : 0);
+        }
+#pragma unroll
+        for (int k = 0; k < 7; k++) ga[k * AT::NG + e] = v[k];
+        gg[e] = g;
+        gf[e] = fl;
+    }
+    __syncthreads();
+    // staged planes; the accumulators start from the update's 4/3 x-bar in the
+    // tile's own cells, whose new x-bar (-1/3 x-bar) is written here
+    for (int r = tid; r < AT::A; r += TX * TY) {
+        const int x = r % AT::W - 1, y = r / AT::W - 1;
+        const int gi = gg[AT::ex(x)], gj = gg[AT::ey(y)];
+        const bool inside = gi >= 0 && gj >= 0;
+        const bool own = x >= 0 && x < TX && y >= 0 && y < TY && i0 + x < I.nx && j0 + y < I.ny;
+        const long long c = inside ? cell_of(I, gi, gj) : 0;
 #pragma unroll
         for (int q = 0; q < Q; q++) {
-            const T xf = Ad.xf[q * N + c], xg = Ad.xg[q * N + c];
-            atomicAdd(Ad.bp + q * N + c, T(4.0 / 3.0) * xf);
-            atomicAdd(Ad.bp + (Q + q) * N + c, T(4.0 / 3.0) * xg);
-            Ad.af[q * N + c] = -T(1.0 / 3.0) * xf;
-            Ad.ag[q * N + c] = -T(1.0 / 3.0) * xg;
+            const T xf = inside ? Ad.xf[q * N + c] : T(0), xg = inside ? Ad.xg[q * N + c] : T(0);
+            in[(AT::BP + q) * AT::A + r] = inside ? P.fbp[q * N + c] : T(0);
+            in[(AT::BP + Q + q) * AT::A + r] = inside ? P.gbp[q * N + c] : T(0);
+            in[(AT::XF + q) * AT::A + r] = xf;
+            in[(AT::XG + q) * AT::A + r] = xg;
+            acc[q * AT::A + r] = own ? T(4.0 / 3.0) * xf : T(0);
+            acc[(Q + q) * AT::A + r] = own ? T(4.0 / 3.0) * xg : T(0);
+            if (own) {
+                Ad.af[q * N + c] = -T(1.0 / 3.0) * xf;
+                Ad.ag[q * N + c] = -T(1.0 / 3.0) * xg;
+            }
         }
-        if (ax.lo_wall) wall_face_adj<T, 0>(I, Pr, P, Ad, geo, i, j, -1, lamb);
-        else interior_face_adj<T, 0>(I, Pr, P, Ad, geo, ax.km, j, i, j, lamb);
-        if (ax.hi_wall) wall_face_adj<T, 0>(I, Pr, P, Ad, geo, i, j, +1, lamb);
-        if (ay.lo_wall) wall_face_adj<T, 1>(I, Pr, P, Ad, geo, i, j, -1, lamb);
-        else interior_face_adj<T, 1>(I, Pr, P, Ad, geo, i, ay.km, i, j, lamb);
-        if (ay.hi_wall) wall_face_adj<T, 1>(I, Pr, P, Ad, geo, i, j, +1, lamb);
+        const T *aux[8] = {P.mu, P.lapmu, P.gmux, P.gmuy, P.gpx, P.gpy, P.gphix, P.gphiy};
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            in[(AT::AUX + k) * AT::A + r] = inside ? aux[k][c] : T(0);
+            acc[(2 * Q + k) * AT::A + r] = T(0);
+        }
+    }
+    __syncthreads();
+    const AdjTileView<T> V{ga, gf, in, acc};
+    T lamb = 0;
+    {
+        const int x = threadIdx.x, y = threadIdx.y;
+        if (i0 + x < I.nx && j0 + y < I.ny) {
+            const int fx = gf[AT::ex(x)], fy = gf[AT::ey(y)];
+            if (fx & 4) wall_face_adj_t<T, 0>(Pr, V, x, y, -1, lamb);
+            else interior_face_adj_t<T, 0>(Pr, V, x - 1, y, x, y, lamb);
+            if (fx & 8) wall_face_adj_t<T, 0>(Pr, V, x, y, +1, lamb);
+            if (fy & 4) wall_face_adj_t<T, 1>(Pr, V, x, y, -1, lamb);
+            else interior_face_adj_t<T, 1>(Pr, V, x, y - 1, x, y, lamb);
+            if (fy & 8) wall_face_adj_t<T, 1>(Pr, V, x, y, +1, lamb);
+        }
+    }
+    __syncthreads();
+    // every accumulator slot of a cell of the domain, added once
+    T *const aux_out[8] = {Ad.mu, Ad.lapmu, Ad.gmx, Ad.gmy, Ad.gpx, Ad.gpy, Ad.gfx, Ad.gfy};
+    for (int r = tid; r < AT::A; r += TX * TY) {
+        const int gi = gg[AT::ex(r % AT::W - 1)], gj = gg[AT::ey(r / AT::W - 1)];
+        if (gi < 0 || gj < 0) continue;
+        const long long c = cell_of(I, gi, gj);
+#pragma unroll
+        for (int k = 0; k < 2 * Q; k++) {
+            const T v = acc[k * AT::A + r];
+            if (v != T(0)) atomicAdd(Ad.bp + k * N + c, v);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const T v = acc[(2 * Q + k) * AT::A + r];
+            if (v != T(0)) atomicAdd(aux_out[k] + c, v);
+        }
     }
     block_add_param(Ad.pk + 2 * t.x, lamb);
 }
@@ -497,7 +593,7 @@ __device__ __forceinline__ void force_adj(const ParT<T> &Pr, T phi, T gmx, T gmy
 
 // bar-plus at the cell centre (Eq. relations1) and its equilibria and sources
 template <typename T>
-__global__ void __launch_bounds__(TX *TY) ka_cell(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles,
+__global__ void __launch_bounds__(TX *TY, sizeof(T) == 4 ? 2 : 1) ka_cell(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles,
                                                   const AxisRec *__restrict__ geo, Planes<T> P, AdjPlanes<T> Ad)
 {
     const int4 t = tiles[blockIdx.x];
@@ -518,17 +614,30 @@ __global__ void __launch_bounds__(TX *TY) ka_cell(const InstDev *__restrict__ in
         PtBar<T> sb = ptbar_zero<T>();
         InvBar<T> vb = invbar_zero<T>();
         T afb = 0, bfb = 0, cfb = 0;
+        // every input of the nine directions is loaded before any store, so
+        // that the loads are in flight together
+        T pf[Q], pg[Q], fv[Q], xa[Q], xg[Q];
 #pragma unroll
         for (int q = 0; q < Q; q++) {
-            const T pf = Ad.bp[q * N + c], pg = Ad.bp[(Q + q) * N + c];
+            pf[q] = Ad.bp[q * N + c];
+            pg[q] = Ad.bp[(Q + q) * N + c];
+            fv[q] = P.f[q * N + c];
+            xa[q] = Ad.af[q * N + c];
+            xg[q] = Ad.ag[q * N + c];
+        }
+#pragma unroll
+        for (int q = 0; q < Q; q++) {
             T feq, geq, Ff, Fg;
             eq_src<T>(s, v, q, feq, geq, Ff, Fg);
-            Ad.af[q * N + c] += af * pf;
-            Ad.ag[q * N + c] += ag * pg;
-            afb += P.f[q * N + c] * pf;
-            bfb += feq * pf;
-            cfb += Ff * pf;
-            eq_src_adj<T>(s, v, q, bf * pf, bg * pg, cf * pf, cg * pg, sb, vb);
+            afb += fv[q] * pf[q];
+            bfb += feq * pf[q];
+            cfb += Ff * pf[q];
+            eq_src_adj<T>(s, v, q, bf * pf[q], bg * pg[q], cf * pf[q], cg * pg[q], sb, vb);
+        }
+#pragma unroll
+        for (int q = 0; q < Q; q++) {
+            Ad.af[q * N + c] = xa[q] + af * pf[q];
+            Ad.ag[q * N + c] = xg[q] + ag * pg[q];
         }
         // af = (2 tf - h) rf, bf = 3 h rf, cf = 3 tf h rf, rf = 1 / (2 tf + dt)
         const T taub = afb * T(3) * dt * rf * rf - bfb * T(6) * h * rf * rf + cfb * T(3) * h * dt * rf * rf;

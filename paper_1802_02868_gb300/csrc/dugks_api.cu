@@ -44,6 +44,8 @@ struct dugks_sim {
     // device
     InstDev *d_inst = nullptr;
     int4 *d_tiles = nullptr;
+    int4 *d_strips8 = nullptr;    // strips of up to DIAG_SB tiles of one tile column (diagnostics)
+    int n_strips8 = 0;
     AxisRec *d_geo = nullptr;
     void *d_geoT = nullptr;       // the same records in the arithmetic type of the sim
     long long *d_dense0 = nullptr;
@@ -104,7 +106,7 @@ const ShapeDesc kShapes[DUGKS_NUM_TILE_SHAPES] = {{32, 8, 256, 0, 0, "32x8"},
                                                   {32, 8, 288, 0, 16, "32x8 strip16/288"},
                                                   {32, 8, 288, 0, 32, "32x8 strip32/288"}};
 
-const char *kNames[K_COUNT] = {"k_mu", "k_macro", "k_cell", "k_face", "k_init", "k_reduce", "k_step", "k_diag"};
+const char *kNames[K_COUNT] = {"k_mu", "k_macro", "k_cell", "k_face", "k_init", "k_reduce", "k_step", "k_diag_f"};
 
 int cuda_status(cudaError_t e)
 {
@@ -563,20 +565,50 @@ int do_unpack_state(dugks_sim *s, const double *src_dev)
     return cuda_status(cudaGetLastError());
 }
 
+// the strip table: {instance, first column, first row, tiles} for strips of
+// up to DIAG_SB tiles of one tile column
+int ensure_strips8(dugks_sim *s)
+{
+    if (s->d_strips8) return DUGKS_OK;
+    std::vector<int4> st;
+    for (int i = 0; i < s->n_inst; i++) {
+        const InstDev &I = s->h_inst[i];
+        const int nty = (I.ny + TY - 1) / TY;
+        for (int tx = 0; tx < I.nx; tx += TX)
+            for (int ty = 0; ty < nty; ty += DIAG_SB) st.push_back(make_int4(i, tx, ty * TY, std::min(DIAG_SB, nty - ty)));
+    }
+    cudaError_t e = dmalloc(s, (void **)&s->d_strips8, sizeof(int4) * st.size());
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_strips8, st.data(), sizeof(int4) * st.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        dfree(s, s->d_strips8);
+        s->d_strips8 = nullptr;
+        return cuda_status(e);
+    }
+    s->n_strips8 = (int)st.size();
+    return DUGKS_OK;
+}
+
 template <typename T>
 int do_reduce(dugks_sim *s)
 {
     Planes<T> &P = planes<T>(s);
     const dim3 blk(TX, TY);
-    // FP32: one warp per tile over a grid of 8 blocks per SM; FP64: a block per tile
-    const unsigned g = sizeof(T) == sizeof(float) ? (unsigned)std::min(s->n_tiles, s->n_sm * 8) : (unsigned)s->n_tiles;
-    { Timed t(s, K_REDUCE); k_reduce<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->n_tiles, s->d_geo, (const AxisRecT<T> *)s->d_geoT, P, s->d_partials); }
+    // FP32: one warp per tile over a grid of as many blocks as the SMs hold at
+    // once; FP64: a block per tile
+    static int resident = 0;
+    if (sizeof(T) == sizeof(float) && resident == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_reduce<T>, TX * TY, 0) != cudaSuccess || resident < 1)
+            resident = 4;
+    }
+    const unsigned g = sizeof(T) == sizeof(float) ? (unsigned)std::min(s->n_tiles, s->n_sm * resident) : (unsigned)s->n_tiles;
+    { Timed t(s, K_REDUCE); k_reduce<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->n_tiles, s->d_geo,
+                                                                   (const AxisRecT<T> *)s->d_geoT, P, s->d_partials); }
     { Timed t(s, -1); k_reduce_inst<<<(s->n_inst + 3) / 4, 128, 0, s->stream>>>(s->d_inst, s->n_inst, s->d_partials, s->d_sums, sizeof(T) == sizeof(float) ? 1 : 0); }
     return cuda_status(cudaGetLastError());
 }
 
-// Diagnostics: macros (k_mu, k_macro), then k_diag per tile (optionally the
-// dense P field into p_dense) and k_diag_inst per instance.
+// Diagnostics: k_diag_f per strip of tiles in one pass over the state
+// (optionally the dense P field into p_dense), then k_diag_inst per instance.
 template <typename T>
 int do_diag(dugks_sim *s, double *p_dense)
 {
@@ -589,13 +621,13 @@ int do_diag(dugks_sim *s, double *p_dense)
             return cuda_status(e);
         }
     }
+    const int rc = ensure_strips8(s);
+    if (rc) return rc;
     Planes<T> &P = planes<T>(s);
     const dim3 blk(TX, TY);
-    const unsigned g = (unsigned)s->n_tiles;
-    { Timed t(s, K_MU); k_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, (const AxisRecT<T> *)s->d_geoT, P); }
-    { Timed t(s, K_MACRO); k_macro<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, (const AxisRecT<T> *)s->d_geoT, P, 0); }
-    { Timed t(s, K_DIAG); k_diag<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, (const AxisRecT<T> *)s->d_geoT, s->d_geo, P,
-                                                                s->d_diag_parts, p_dense, s->d_dense0); }
+    const unsigned g = (unsigned)s->n_strips8;
+    { Timed t(s, K_DIAG); k_diag_f<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_strips8, (const AxisRecT<T> *)s->d_geoT, s->d_geo, P,
+                                                                  s->d_diag_parts, p_dense, s->d_dense0); }
     { Timed t(s, -1); k_diag_inst<<<(unsigned)s->n_inst, DIAG_INST_THREADS, 0, s->stream>>>(s->d_inst, s->d_status, s->d_diag_parts, s->d_diag_out); }
     return cuda_status(cudaGetLastError());
 }
@@ -628,6 +660,7 @@ void free_sim(dugks_sim *s)
     dfree(s, s->d_inst);
     dfree(s, s->d_tiles);
     for (int k = 0; k < DUGKS_NUM_TILE_SHAPES; k++) dfree(s, s->d_tiles_s[k]);
+    dfree(s, s->d_strips8);
     dfree(s, s->d_geo);
     dfree(s, s->d_geoT);
     dfree(s, s->d_dense0);
@@ -693,6 +726,13 @@ int adjoint_impl(dugks_sim *s, long nsteps, int K, const double *target_h, doubl
     const int n = s->n_inst;
     const dim3 blk(TX, TY);
     const unsigned g = (unsigned)s->n_tiles;
+    static bool attr_set = false;   // per precision; the tiled face transpose takes more than 48 KB of shared memory
+    if (!attr_set) {
+        const cudaError_t e0 = cudaFuncSetAttribute(ka_face_t<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                    (int)AdjTile<T>::bytes);
+        if (e0 != cudaSuccess) return cuda_status(e0);
+        attr_set = true;
+    }
     AdjWork<T> w;
     w.fg_bytes = sizeof(T) * 2 * Q * (size_t)N;
     w.phi_bytes = sizeof(phi_t<T>) * (size_t)N;
@@ -768,7 +808,8 @@ int adjoint_impl(dugks_sim *s, long nsteps, int K, const double *target_h, doubl
             cudaMemsetAsync(w.scal, 0, sizeof(T) * scal_planes * (size_t)N, s->stream);
             A.xf = xb; A.xg = xb + (size_t)Q * N;
             A.af = xn; A.ag = xn + (size_t)Q * N;
-            ka_face<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, A);
+            ka_face_t<T><<<g, blk, AdjTile<T>::bytes, s->stream>>>(s->d_inst, s->d_tiles, (const AxisRecT<T> *)s->d_geoT,
+                                                                  P, A);
             ka_cell<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, A);
             ka_macro<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, A);
             ka_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, A);
@@ -1287,7 +1328,7 @@ int dugks_kernel_bytes_per_cell(const dugks_sim *s, int k, double *bytes)
     case K_INIT: b = 8 + 4 * w + 18 * w; break;
     case K_REDUCE: b = 8; break;
     case K_STEP: b = 2 * (2 * Q) * w + 16; break;                   // tilde f, g and phi, read once and written once
-    case K_DIAG: b = 8 + 3 * w; break;                               // phi, p, ux, uy (the P field adds 8 written)
+    case K_DIAG: b = 8 + 9 * w; break;                               // phi, tilde f (the P field adds 8 written)
     }
     *bytes = b;
     return DUGKS_OK;

@@ -691,11 +691,10 @@ __device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, f
 // k_reduce: per-tile partial sums of |V| phi and |V| rho; a second pass
 // (k_reduce_inst) adds the partials of each instance in tile order.  FP64
 // sims: one thread block per tile, sums in FP64.  FP32 sims: one warp per
-// tile over a grid of a few blocks per SM (a block per tile spends most of
-// its time starting and retiring); each lane adds dx dy phi of its column in
-// double-float, the lanes are added in a fixed tree, and the sum is
-// converted once per tile (a warp-wide FP64 instruction occupies GB300's FP64
-// pipe for 16 cycles even with one lane active).
+// tile over a grid of the blocks the SMs hold at once; each lane adds dx dy
+// phi of its column in double-float, the lanes are added in a fixed tree, and
+// the sum is converted once per tile (a warp-wide FP64 instruction occupies
+// GB300's FP64 pipe for 16 cycles even with one lane active).
 // Their |V| rho sum is formed per instance from sum |V| phi, because rho is
 // linear in phi (Eq. oderrho): sum |V| rho = rhoB V + (drho)(sum |V| phi - phiB V).
 template <typename T>
@@ -711,24 +710,34 @@ __global__ void __launch_bounds__(TX *TY) k_reduce(const InstDev *__restrict__ i
             const int4 t = tiles[tt];
             const InstDev &I = insts[t.x];
             const int i = t.y + lane;
-            // each lane adds dx dy phi of its column over the tile's rows, then
-            // the lanes are added in a fixed tree
-            float ah = 0.f, al = 0.f;
-            if (i < I.nx) {
+            // every load of the tile first (the column's phi pairs and the row
+            // widths), so that they are in flight together; then each lane
+            // adds dx dy phi of its column, and the lanes are added in a
+            // fixed tree
+            const bool col = i < I.nx;
+            float2 ph[TY];
+            float dyh[TY], dyl[TY];
+            float dxh = 0.f, dxl = 0.f;
+            if (col) {
                 const AxisRecT<float> &ax = geoT[I.gx_off + i];
-                const float dxh = ax.d, dxl = ax.d_lo;
+                dxh = ax.d;
+                dxl = ax.d_lo;
+            }
 #pragma unroll
-                for (int r = 0; r < TY; r++) {
-                    const int j = t.z + r;
-                    if (j < I.ny) {
-                        const float2 p = P.phi[cell_of(I, i, j)];
-                        const AxisRecT<float> &ay = geoT[I.gy_off + j];
-                        float vh, vl, ch, cl;
-                        ff_mul(dxh, dxl, ay.d, ay.d_lo, vh, vl);
-                        ff_mul(vh, vl, p.x, p.y, ch, cl);
-                        ff_sum(ah, al, ch, cl, ah, al);
-                    }
-                }
+            for (int r = 0; r < TY; r++) {
+                const int j = t.z + r;
+                const bool ok = col && j < I.ny;
+                ph[r] = ok ? P.phi[cell_of(I, i, j)] : make_float2(0.f, 0.f);
+                dyh[r] = ok ? geoT[I.gy_off + j].d : 0.f;
+                dyl[r] = ok ? geoT[I.gy_off + j].d_lo : 0.f;
+            }
+            float ah = 0.f, al = 0.f;
+#pragma unroll
+            for (int r = 0; r < TY; r++) {
+                float vh, vl, ch, cl;
+                ff_mul(dxh, dxl, dyh[r], dyl[r], vh, vl);
+                ff_mul(vh, vl, ph[r].x, ph[r].y, ch, cl);
+                ff_sum(ah, al, ch, cl, ah, al);
             }
             for (int o = 16; o > 0; o >>= 1) {
                 const float oh = __shfl_down_sync(0xffffffffu, ah, o), ol = __shfl_down_sync(0xffffffffu, al, o);
