@@ -49,9 +49,9 @@ PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # tile shape, from ncu captures of a 2048 x 2048 periodic drop
 # (dram__bytes_read.sum + dram__bytes_write.sum over 4,194,304 cells); valid
 # only for the kernel sources they were taken on.
-TRAFFIC_SOURCES_SHA = "271c4ff2eda049cb"
+TRAFFIC_SOURCES_SHA = "90ab830e5f87019c"
 TRAFFIC_BYTES_PER_CELL_FP32 = {
-    "32x8 strip16/288": (347.206912e6 + 296.959232e6) / 4194304,
+    "32x8 strip16/288": (347.191808e6 + 296.941312e6) / 4194304,
 }
 
 
@@ -438,7 +438,11 @@ def main():
             "measured_fma_tflops": meas,
             "flop_per_cell": FLOP_PER_CELL_UPDATE, "traffic": traffic, "avg_launch_ms": avg_s * 1e3,
             "hbm": {"achieved": hbm_achieved, "peak": peak_hbm, "unit": "GB/s", "frac": hbm_achieved / peak_hbm,
-                    "peak_source": peak_kind, "algorithmic_bytes_per_cell": bpc},
+                    "peak_source": peak_kind, "algorithmic_bytes_per_cell": bpc,
+                    # the state alone: 18 tilde words read and written; the fused
+                    # step also reads and writes the stored phi (a float pair in FP32)
+                    "state_bytes_per_cell": 2 * 18 * (4 if prec == dugks.FP32 else 8),
+                    "frac_state_bytes": (2 * 18 * (4 if prec == dugks.FP32 else 8)) * ncells / avg_s / 1e9 / peak_hbm},
             "kernel_share": {k: v[0] / max(sum(x[0] for x in ktimes.values()), 1e-12) for k, v in ktimes.items()
                              if v[1]}}
 
