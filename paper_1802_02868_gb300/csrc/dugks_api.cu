@@ -518,20 +518,22 @@ int do_init(dugks_sim *s)
     return cuda_status(cudaGetLastError());
 }
 
+// dst[0..4]: where phi, rho, ux, uy, p go (device-visible pointers, NULL to
+// skip one): the staging buffer, or the caller's pinned host memory itself.
 template <typename T>
-int do_moments(dugks_sim *s)
+int do_moments(dugks_sim *s, double *const dst[5])
 {
     Planes<T> &P = planes<T>(s);
     const dim3 blk(TX, TY);
     const unsigned g = (unsigned)s->n_tiles;
-    const long long D = s->n_dense;
     { Timed t(s, K_MU); k_mu<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, (const AxisRecT<T> *)s->d_geoT, P); }
     { Timed t(s, K_MACRO); k_macro<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, (const AxisRecT<T> *)s->d_geoT, P, 1); }
-    { Timed t(s, -1); k_pack_phi<phi_t<T>><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, P.phi, s->d_stage, s->d_dense0); }
+    if (dst[0]) { Timed t(s, -1); k_pack_phi<phi_t<T>><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, P.phi, dst[0], s->d_dense0); }
     T *src[4] = {P.rho, P.ux, P.uy, P.p};
     for (int k = 0; k < 4; k++) {
+        if (!dst[k + 1]) continue;
         Timed t(s, -1);
-        k_pack<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, src[k], s->d_stage + (k + 1) * D, s->d_dense0);
+        k_pack<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, src[k], dst[k + 1], s->d_dense0);
     }
     return cuda_status(cudaGetLastError());
 }
@@ -863,6 +865,19 @@ int adjoint_impl(dugks_sim *s, long nsteps, int K, const double *target_h, doubl
     return rc;
 }
 
+// The device address through which kernels may write the host array p: set
+// for page-locked memory (cudaHostAlloc, cudaHostRegister, which unified
+// addressing maps into the device's address space); NULL for pageable memory.
+double *host_alias(double *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? static_cast<double *>(a.devicePointer) : nullptr;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1067,14 +1082,26 @@ int dugks_init(dugks_sim *s, const double *phi, const double *ux, const double *
 {
     if (!s || !phi) return DUGKS_ERR_ARG;
     const long long D = s->n_dense;
-    for (long long c = 0; c < D; c++) if (!std::isfinite(phi[c])) return DUGKS_ERR_NONFINITE;
     const double *src[4] = {phi, ux, uy, p};
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < 4 && e == cudaSuccess; k++) {
         if (src[k]) e = cudaMemcpyAsync(s->d_stage + k * D, src[k], sizeof(double) * D, cudaMemcpyHostToDevice, s->stream);
         else e = cudaMemsetAsync(s->d_stage + k * D, 0, sizeof(double) * D, s->stream);
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(s->d_status, 0, sizeof(int) * s->n_inst, s->stream);
+    // a non-finite phi is refused before any state changes: checked on the
+    // uploaded copy (the staging buffer is scratch), the flag in the reduction
+    // scratch, which no call holds across this one
+    int *flag = reinterpret_cast<int *>(s->d_partials), bad = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(flag, 0, sizeof(int), s->stream);
+    if (e == cudaSuccess) {
+        { Timed t(s, -1); k_any_nonfinite<<<(unsigned)(s->n_sm * 8), 256, 0, s->stream>>>(s->d_stage, D, flag); }
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (bad) return DUGKS_ERR_NONFINITE;
+    e = cudaMemsetAsync(s->d_status, 0, sizeof(int) * s->n_inst, s->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(s->d_init_in, s->d_stage, sizeof(double) * 4 * D, cudaMemcpyDeviceToDevice, s->stream);
     if (e != cudaSuccess) return cuda_status(e);
     int rc = s->prec == DUGKS_FP64 ? do_init<double>(s) : do_init<float>(s);
@@ -1097,13 +1124,20 @@ int dugks_step(dugks_sim *s, long nsteps)
 int dugks_moments(dugks_sim *s, double *phi, double *rho, double *ux, double *uy, double *p)
 {
     if (!s) return DUGKS_ERR_ARG;
-    int rc = s->prec == DUGKS_FP64 ? do_moments<double>(s) : do_moments<float>(s);
-    if (rc) return rc;
     const long long D = s->n_dense;
-    double *dst[5] = {phi, rho, ux, uy, p};
+    double *out[5] = {phi, rho, ux, uy, p};
+    // page-locked outputs are written by the gather kernels themselves over
+    // the host link; the others through the staging buffer and a copy
+    double *dst[5], *alias[5];
     for (int k = 0; k < 5; k++) {
-        if (!dst[k]) continue;
-        cudaError_t e = cudaMemcpyAsync(dst[k], s->d_stage + k * D, sizeof(double) * D, cudaMemcpyDeviceToHost, s->stream);
+        alias[k] = out[k] ? host_alias(out[k]) : nullptr;
+        dst[k] = !out[k] ? nullptr : alias[k] ? alias[k] : s->d_stage + k * D;
+    }
+    int rc = s->prec == DUGKS_FP64 ? do_moments<double>(s, dst) : do_moments<float>(s, dst);
+    if (rc) return rc;
+    for (int k = 0; k < 5; k++) {
+        if (!out[k] || alias[k]) continue;
+        cudaError_t e = cudaMemcpyAsync(out[k], dst[k], sizeof(double) * D, cudaMemcpyDeviceToHost, s->stream);
         if (e != cudaSuccess) return cuda_status(e);
     }
     return sync_status(s);

@@ -818,6 +818,17 @@ __global__ void k_unpack_phi(const InstDev *__restrict__ insts, const int4 *__re
     phi_from_double(src[dense0[t.x] + (long long)j * I.nx + i], dst[cell_of(I, i, j)]);
 }
 
+// Set *flag (zeroed by the caller) when a[0..n) holds a non-finite value: the
+// init inputs are checked on the device after the upload, one pass at HBM
+// speed, instead of by a host loop over the caller's array.
+__global__ void k_any_nonfinite(const double *__restrict__ a, long long n, int *flag)
+{
+    bool bad = false;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x)
+        bad |= !isfinite(a[c]);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
+}
+
 // Gather a padded plane (type T) into a dense double array and back.
 template <typename T>
 __global__ void k_pack(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles, const T *__restrict__ src,
