@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -73,6 +74,8 @@ struct dugks_sim {
     cudaGraphExec_t graph2 = nullptr;   // k_step(A -> B), k_step(B -> A)
     int *d_status = nullptr;
     double2 *d_partials = nullptr;
+    RedTile *d_red = nullptr;     // FP32 sims: one record per tile for the conservation sums
+    float2 *d_redgeo = nullptr;   // FP32 sims: the widths {d, d_lo} of the geometry records
     double2 *d_sums = nullptr;
     double *d_stage = nullptr;    // dense FP64 staging [5][n_dense]
     double *d_init_in = nullptr;  // the last init inputs phi, ux, uy, p [4][n_dense] (for the adjoint)
@@ -597,14 +600,18 @@ int do_reduce(dugks_sim *s)
     const dim3 blk(TX, TY);
     // FP32: one warp per tile over a grid of as many blocks as the SMs hold at
     // once; FP64: a block per tile
-    static int resident = 0;
-    if (sizeof(T) == sizeof(float) && resident == 0) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_reduce<T>, TX * TY, 0) != cudaSuccess || resident < 1)
+    if constexpr (sizeof(T) == sizeof(float)) {
+        static int resident = 0;
+        if (resident == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&resident, k_reduce_f32, 256, 0) != cudaSuccess ||
+                              resident < 1))
             resident = 4;
+        const unsigned g = (unsigned)std::min((s->n_tiles + 7) / 8, s->n_sm * resident);
+        Timed t(s, K_REDUCE);
+        k_reduce_f32<<<g, 256, 0, s->stream>>>(s->d_red, s->n_tiles, s->d_redgeo, (const float2 *)P.phi, s->d_partials);
+    } else {
+        Timed t(s, K_REDUCE);
+        k_reduce<T><<<(unsigned)s->n_tiles, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->d_geo, P, s->d_partials);
     }
-    const unsigned g = sizeof(T) == sizeof(float) ? (unsigned)std::min(s->n_tiles, s->n_sm * resident) : (unsigned)s->n_tiles;
-    { Timed t(s, K_REDUCE); k_reduce<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_tiles, s->n_tiles, s->d_geo,
-                                                                   (const AxisRecT<T> *)s->d_geoT, P, s->d_partials); }
     { Timed t(s, -1); k_reduce_inst<<<(s->n_inst + 3) / 4, 128, 0, s->stream>>>(s->d_inst, s->n_inst, s->d_partials, s->d_sums, sizeof(T) == sizeof(float) ? 1 : 0); }
     return cuda_status(cudaGetLastError());
 }
@@ -672,6 +679,8 @@ void free_sim(dugks_sim *s)
     dfree(s, s->d_phi_alt_alloc);
     dfree(s, s->d_status);
     dfree(s, s->d_partials);
+    dfree(s, s->d_red);
+    dfree(s, s->d_redgeo);
     dfree(s, s->d_sums);
     dfree(s, s->d_stage);
     dfree(s, s->d_init_in);
@@ -1037,6 +1046,27 @@ int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *para
     s->d_phi_alt = s->d_phi_alt_alloc;
     chk(dmalloc(s, (void **)&s->d_status, sizeof(int) * n));
     chk(dmalloc(s, (void **)&s->d_partials, sizeof(double2) * tiles.size()));
+    // FP32 sims: the conservation sums' tile records and compact widths
+    std::vector<RedTile> red;
+    std::vector<float2> redgeo;
+    if (!is64) {
+        if (geo.size() > (size_t)INT_MAX) e = cudaErrorInvalidValue;
+        for (const int4 &t : tiles) {
+            const InstDev &I = s->h_inst[t.x];
+            RedTile r;
+            r.c0 = I.cell0 + (long long)t.z * I.nxp + t.y;
+            r.gx = (int)(I.gx_off + t.y);
+            r.gy = (int)(I.gy_off + t.z);
+            r.pitch = I.nxp;
+            r.ncol = std::min(TX, I.nx - t.y);
+            r.nrow = std::min(TY, I.ny - t.z);
+            r.pad = 0;
+            red.push_back(r);
+        }
+        for (const AxisRecT<float> &b : g32) redgeo.push_back(make_float2(b.d, b.d_lo));
+        chk(dmalloc(s, (void **)&s->d_red, sizeof(RedTile) * red.size()));
+        chk(dmalloc(s, (void **)&s->d_redgeo, sizeof(float2) * redgeo.size()));
+    }
     chk(dmalloc(s, (void **)&s->d_sums, sizeof(double2) * n));
     chk(dmalloc(s, (void **)&s->d_stage, sizeof(double) * (size_t)std::max<long long>(5, 2 * Q) * (size_t)dense));
     chk(dmalloc(s, (void **)&s->d_init_in, sizeof(double) * 4 * (size_t)dense));
@@ -1050,6 +1080,10 @@ int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *para
     chk(cudaMemcpy(s->d_geo, geo.data(), sizeof(AxisRec) * geo.size(), cudaMemcpyHostToDevice));
     chk(cudaMemcpy(s->d_geoT, is64 ? (const void *)g64.data() : (const void *)g32.data(), geoT_bytes, cudaMemcpyHostToDevice));
     chk(cudaMemcpy(s->d_dense0, s->h_dense0.data(), sizeof(long long) * n, cudaMemcpyHostToDevice));
+    if (!is64) {
+        chk(cudaMemcpy(s->d_red, red.data(), sizeof(RedTile) * red.size(), cudaMemcpyHostToDevice));
+        chk(cudaMemcpy(s->d_redgeo, redgeo.data(), sizeof(float2) * redgeo.size(), cudaMemcpyHostToDevice));
+    }
     chk(cudaMemset(s->d_planes, 0, esz * plane_elems));
     chk(cudaMemset(s->d_phi, 0, sizeof(double) * (size_t)s->N));
     chk(cudaMemset(s->d_alt_alloc, 0, esz * 2 * Q * (size_t)s->N));

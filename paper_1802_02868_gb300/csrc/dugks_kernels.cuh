@@ -8,7 +8,7 @@
 //   k_face  : face reconstruction, face macros, originals, flux,
 //             tilde update in place, phi = sum g for the next step (Eqs. fbar_h, original-function,
 //                                                                   microfluxf, updatef, relations2)
-// plus k_init (step 1) and k_reduce (FP64 conservation sums).
+// plus k_init (step 1) and k_reduce / k_reduce_f32 (FP64 conservation sums).
 #pragma once
 #include "dugks_common.cuh"
 
@@ -663,9 +663,18 @@ __global__ void __launch_bounds__(TX *TY) k_phi(const InstDev *__restrict__ inst
 }
 
 // ---------------------------------------------------------------------------
-// k_reduce: per-tile FP64 partial sums of |V| phi and |V| rho; a second pass
-// (k_reduce_inst) adds the partials of each instance in tile order.
+// Conservation sums (Eq. locallyconserved): per-tile FP64 partials of |V| phi
+// and |V| rho (k_reduce for FP64 sims, k_reduce_f32 for FP32 sims); a second
+// pass (k_reduce_inst) adds the partials of each instance in tile order.
 // ---------------------------------------------------------------------------
+// One record per tile for the FP32 conservation sums (k_reduce_f32): the
+// cell of the tile's first column and row, the first x and y geometry records,
+// the instance's row pitch, and the tile's valid columns and rows.
+struct __align__(16) RedTile {
+    long long c0;
+    int gx, gy, pitch, ncol, nrow, pad;
+};
+
 // Double-float arithmetic for the FP32 sums: a value is an unevaluated pair
 // hi + lo of floats.  ff_sum is Knuth's TwoSum, ff_mul Dekker's product with
 // the FMA giving the exact error of hi * hi; both keep about 48 bits, the
@@ -688,87 +697,84 @@ __device__ __forceinline__ void ff_mul(float ah, float al, float bh, float bl, f
     pl = __fsub_rn(e, __fsub_rn(ph, p));
 }
 
-// k_reduce: per-tile partial sums of |V| phi and |V| rho; a second pass
-// (k_reduce_inst) adds the partials of each instance in tile order.  FP64
-// sims: one thread block per tile, sums in FP64.  FP32 sims: one warp per
-// tile over a grid of the blocks the SMs hold at once; each lane adds dx dy
-// phi of its column in double-float, the lanes are added in a fixed tree, and
-// the sum is converted once per tile (a warp-wide FP64 instruction occupies
-// GB300's FP64 pipe for 16 cycles even with one lane active).
-// Their |V| rho sum is formed per instance from sum |V| phi, because rho is
-// linear in phi (Eq. oderrho): sum |V| rho = rhoB V + (drho)(sum |V| phi - phiB V).
+// k_reduce: per-tile partial sums of |V| phi and |V| rho of FP64 sims, one
+// thread block per tile; a second pass (k_reduce_inst) adds the partials of
+// each instance in tile order.
 template <typename T>
 __global__ void __launch_bounds__(TX *TY) k_reduce(const InstDev *__restrict__ insts, const int4 *__restrict__ tiles,
-                                                   int n_tiles, const AxisRec *__restrict__ geo,
-                                                   const AxisRecT<T> *__restrict__ geoT, Planes<T> P, double2 *partials)
+                                                   const AxisRec *__restrict__ geo, Planes<T> P, double2 *partials)
 {
     const int lane = (threadIdx.y * TX + threadIdx.x) & 31, warp = (threadIdx.y * TX + threadIdx.x) >> 5;
-    if constexpr (sizeof(T) == sizeof(float)) {
-        static_assert(TX == 32, "one tile column per lane");
-        const int nw = gridDim.x * (TX * TY / 32);
-        for (int tt = blockIdx.x * (TX * TY / 32) + warp; tt < n_tiles; tt += nw) {
-            const int4 t = tiles[tt];
-            const InstDev &I = insts[t.x];
-            const int i = t.y + lane;
-            // every load of the tile first (the column's phi pairs and the row
-            // widths), so that they are in flight together; then each lane
-            // adds dx dy phi of its column, and the lanes are added in a
-            // fixed tree
-            const bool col = i < I.nx;
-            float2 ph[TY];
-            float dyh[TY], dyl[TY];
-            float dxh = 0.f, dxl = 0.f;
-            if (col) {
-                const AxisRecT<float> &ax = geoT[I.gx_off + i];
-                dxh = ax.d;
-                dxl = ax.d_lo;
-            }
+    __shared__ double2 red[TX * TY / 32];
+    const int4 t = tiles[blockIdx.x];
+    const InstDev &I = insts[t.x];
+    const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
+    double a = 0.0, b = 0.0;
+    if (i < I.nx && j < I.ny) {
+        const long long c = cell_of(I, i, j);
+        const double phi = phi_to_double(P.phi[c]);
+        double vol = geo[I.gx_off + i].d * geo[I.gy_off + j].d;
+        a = vol * phi;
+        b = vol * (I.rhoB + I.drho * (phi - I.phiB));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) red[warp] = make_double2(a, b);
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        double2 s = red[0];
+        for (int w = 1; w < TX * TY / 32; w++) { s.x += red[w].x; s.y += red[w].y; }
+        partials[blockIdx.x] = s;
+    }
+}
+
+// The FP32 sims' sums |V| phi, one warp per tile over a grid of the blocks the
+// SMs hold at once.  Each tile has one record (RedTile) with the addresses the
+// warp needs, so a tile costs one dependent load before its data, and the next
+// record is in flight while a tile is summed.  Lane l holds column l: it adds
+// dy_r phi_r over the tile's rows in double-float, multiplies the sum by its
+// dx once, and the lanes are added in a fixed tree; the sum is converted to
+// FP64 once per tile (a warp-wide FP64 instruction occupies GB300's FP64 pipe
+// for 16 cycles even with one lane active).  gd: the widths {d, d_lo} of the
+// geometry records.  Their |V| rho sum is formed per instance from sum |V| phi,
+// because rho is linear in phi (Eq. oderrho): sum |V| rho = rhoB V + drho
+// (sum |V| phi - phiB V).
+__global__ void __launch_bounds__(256) k_reduce_f32(const RedTile *__restrict__ rt, int n_tiles,
+                                                    const float2 *__restrict__ gd, const float2 *__restrict__ phi,
+                                                    double2 *__restrict__ partials)
+{
+    const int lane = threadIdx.x & 31;
+    const int nw = gridDim.x * (blockDim.x >> 5);
+    int tt = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (tt >= n_tiles) return;
+    RedTile t = rt[tt];
+    for (; tt < n_tiles; tt += nw) {
+        const RedTile nt = rt[tt + nw < n_tiles ? tt + nw : tt];
+        const bool col = lane < t.ncol;
+        const float2 dx = col ? gd[t.gx + lane] : make_float2(0.f, 0.f);
+        float2 ph[TY], dy[TY];
 #pragma unroll
-            for (int r = 0; r < TY; r++) {
-                const int j = t.z + r;
-                const bool ok = col && j < I.ny;
-                ph[r] = ok ? P.phi[cell_of(I, i, j)] : make_float2(0.f, 0.f);
-                dyh[r] = ok ? geoT[I.gy_off + j].d : 0.f;
-                dyl[r] = ok ? geoT[I.gy_off + j].d_lo : 0.f;
-            }
-            float ah = 0.f, al = 0.f;
+        for (int r = 0; r < TY; r++) {
+            const bool row = r < t.nrow;
+            ph[r] = col && row ? phi[t.c0 + (long long)r * t.pitch + lane] : make_float2(0.f, 0.f);
+            dy[r] = row ? gd[t.gy + r] : make_float2(0.f, 0.f);
+        }
+        float ah = 0.f, al = 0.f;
 #pragma unroll
-            for (int r = 0; r < TY; r++) {
-                float vh, vl, ch, cl;
-                ff_mul(dxh, dxl, dyh[r], dyl[r], vh, vl);
-                ff_mul(vh, vl, ph[r].x, ph[r].y, ch, cl);
-                ff_sum(ah, al, ch, cl, ah, al);
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const float oh = __shfl_down_sync(0xffffffffu, ah, o), ol = __shfl_down_sync(0xffffffffu, al, o);
-                ff_sum(ah, al, oh, ol, ah, al);
-            }
-            if (lane == 0) partials[tt] = make_double2((double)ah + (double)al, 0.0);
+        for (int r = 0; r < TY; r++) {
+            float ch, cl;
+            ff_mul(dy[r].x, dy[r].y, ph[r].x, ph[r].y, ch, cl);
+            ff_sum(ah, al, ch, cl, ah, al);
         }
-    } else {
-        __shared__ double2 red[TX * TY / 32];
-        const int4 t = tiles[blockIdx.x];
-        const InstDev &I = insts[t.x];
-        const int i = t.y + threadIdx.x, j = t.z + threadIdx.y;
-        double a = 0.0, b = 0.0;
-        if (i < I.nx && j < I.ny) {
-            const long long c = cell_of(I, i, j);
-            const double phi = phi_to_double(P.phi[c]);
-            double vol = geo[I.gx_off + i].d * geo[I.gy_off + j].d;
-            a = vol * phi;
-            b = vol * (I.rhoB + I.drho * (phi - I.phiB));
-        }
+        ff_mul(ah, al, dx.x, dx.y, ah, al);
         for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_down_sync(0xffffffffu, a, o);
-            b += __shfl_down_sync(0xffffffffu, b, o);
+            const float oh = __shfl_down_sync(0xffffffffu, ah, o), ol = __shfl_down_sync(0xffffffffu, al, o);
+            ff_sum(ah, al, oh, ol, ah, al);
         }
-        if (lane == 0) red[warp] = make_double2(a, b);
-        __syncthreads();
-        if (threadIdx.x == 0 && threadIdx.y == 0) {
-            double2 s = red[0];
-            for (int w = 1; w < TX * TY / 32; w++) { s.x += red[w].x; s.y += red[w].y; }
-            partials[blockIdx.x] = s;
-        }
+        if (lane == 0) partials[tt] = make_double2((double)ah + (double)al, 0.0);
+        t = nt;
     }
 }
 

@@ -155,6 +155,59 @@ def test_invalid_init_input_rejected():
         s.init(phi)
 
 
+@pytest.mark.parametrize("bad", [math.nan, math.inf, -math.inf])
+def test_rejected_init_leaves_the_state_untouched(bad):
+    """The finiteness check runs on the device over every uploaded value (the
+    last cell of the last instance included); a refused init changes neither
+    the state nor the status, and the sim steps on as before."""
+    cases = [I.stationary_drop(n=24, radius=6.0), I.rayleigh_taylor(nx=16, ny=40, amplitudes=[1.6])]
+    s = dugks.Sim([c.mesh for c in cases], [c.params for c in cases], dugks.FP32)
+    s.init([c.phi0 for c in cases]).step(3)
+    f0, g0 = s.state()
+    for k, (j, i) in ((0, (0, 0)), (1, (39, 15)), (1, (17, 5))):
+        phis = [c.phi0.copy() for c in cases]
+        phis[k][j, i] = bad
+        with pytest.raises(dugks.NonFiniteError):
+            s.init(phis)
+        f1, g1 = s.state()
+        assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
+        assert s.status() == [0, 0]
+    ref = dugks.Sim([c.mesh for c in cases], [c.params for c in cases], dugks.FP32)
+    ref.init([c.phi0 for c in cases]).step(5)
+    s.step(2)
+    assert np.array_equal(s.state()[0], ref.state()[0])
+
+
+def test_moments_into_page_locked_buffers_match_pageable_ones():
+    """Page-locked outputs are written by the gather kernels over the host
+    link, pageable ones through the staging copy: the values are the same
+    bit for bit, for buffers at an offset inside a pinned allocation too, and
+    NULL outputs are skipped."""
+    torch = pytest.importorskip("torch")
+    cases = [I.stationary_drop(n=40, radius=10.0), I.rayleigh_taylor(nx=24, ny=72, amplitudes=[2.4])]
+    s = dugks.Sim([c.mesh for c in cases], [c.params for c in cases], dugks.FP32)
+    s.init([c.phi0 for c in cases]).step(4)
+    ref = s.moments()
+    n = s.ncells
+    base = torch.zeros(5 * n + 1, dtype=torch.float64).pin_memory()
+    views = [base[1 + k * n:1 + (k + 1) * n].numpy() for k in range(5)]   # 8-byte offset into the block
+    got = s.moments(out=views)
+    for key in ("phi", "rho", "ux", "uy", "p"):
+        for a, b in zip(got[key], ref[key]):
+            assert np.array_equal(a, b), key
+    # pinned, pageable and skipped outputs in one call
+    mixed = [views[0], np.zeros(n), None, views[3], None]
+    for v in (views[0], views[3]):
+        v[:] = 0.0
+    L = dugks.load()
+    rc = L.dugks_moments(s.h, *[None if a is None else dugks._dp(a) for a in mixed])
+    assert rc == 0
+    flat = {k: np.concatenate([x.reshape(-1) for x in ref[k]]) for k in ref}
+    assert np.array_equal(mixed[0], flat["phi"]) and np.array_equal(mixed[1], flat["rho"])
+    assert np.array_equal(mixed[3], flat["uy"])
+    s.close()
+
+
 @pytest.mark.parametrize("prec", [dugks.FP64, dugks.FP32])
 def test_fused_step_matches_four_kernel_step(prec, monkeypatch):
     """The one-launch tiled step and the four-kernel step compute the same scheme."""
