@@ -788,9 +788,13 @@ __global__ void k_reduce_inst(const InstDev *__restrict__ insts, int n_inst, con
     if (k >= n_inst) return;
     const InstDev &I = insts[k];
     double2 s = make_double2(0.0, 0.0);
+    // unrolled so that several partials are in flight; the additions keep
+    // their order
+#pragma unroll 8
     for (int t = lane; t < I.ntiles; t += 32) {
-        s.x += partials[I.tile0 + t].x;
-        s.y += partials[I.tile0 + t].y;
+        const double2 v = partials[I.tile0 + t];
+        s.x += v.x;
+        s.y += v.y;
     }
     for (int o = 16; o > 0; o >>= 1) {
         s.x += __shfl_down_sync(0xffffffffu, s.x, o);
