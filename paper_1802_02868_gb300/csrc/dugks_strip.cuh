@@ -11,7 +11,7 @@
 // computes the bottom rows of the first block's rings.  Shared memory does not
 // grow with the strip length.  The thread count NT is chosen so that the new
 // rows of a phase fill whole passes of the threads (with BX = 32, BY = 8 and
-// 288 threads: p 288 items, bar-plus 272, faces 520 in two passes).
+// 288 threads: p 288 items, bar-plus 272, the 520 faces in two passes).
 //
 // Loads of a later block overlap the work of the one before: its new phi rows
 // are copied into a staging area while the faces and the update run, and its
@@ -27,8 +27,17 @@ template <typename T, int BX, int BY>
 struct StripLayout {
     using L = FusedLayout<T, BX, BY, false>;
     static_assert(BY == 8, "the shifted ring rows are the rows that the next block's new rows replace");
+    // face items of a block, in the order the threads take them and the flux
+    // buffer stores them: the x faces on the pitch of the R1 planes (XP items
+    // a row, the last one idle), so that a warp's faces read consecutive R1
+    // entries across a row change; then, from item Y0 (a whole number of
+    // warps), the y faces one row of BX per warp.  Either way no warp reads
+    // two R1 entries of one shared-memory bank.
+    static constexpr int XP = BX + 2;
+    static constexpr int NXI = XP * BY;
+    static constexpr int Y0 = (NXI + 31) / 32 * 32;
     static constexpr int NFY = BX * BY;                   // y faces per block (the bottom row is carried)
-    static constexpr int NFT = L::NFX + NFY;
+    static constexpr int NFT = Y0 + NFY;
     static constexpr int FROWS = BY + 1, GROWS = BY;      // staged tilde rows of a block (f: 1..BY+1, g: 1..BY)
     static constexpr size_t al(size_t v) { return (v + 15) / 16 * 16; }
     static constexpr size_t o_un = L::o_un;               // after the R1 planes
@@ -55,7 +64,7 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
     T *stf = (T *)(smem + SL::o_st);                      // staged tilde f [Q][FROWS][W2]
     T *stg = stf + Q * SL::FROWS * L::W2;                 // staged tilde g [Q][GROWS][W1]
     phi_t<T> *phst = (phi_t<T> *)(smem + SL::o_phst);    // staged phi rows 4 .. BY + 3 of the next block
-    pair_t<T> *flux = (pair_t<T> *)(smem + SL::o_un);    // [6][NFT]
+    pair_t<T> *flux = (pair_t<T> *)(smem + SL::o_un);    // [6][NFT], by face item
     // two [6][BX] buffers: block b reads its bottom y faces from buffer b % 2
     // and leaves its top y faces, the next block's bottom ones, in the other
     pair_t<T> *const keep0 = (pair_t<T> *)(smem + SL::o_keep);
@@ -359,9 +368,17 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
         const int nf = SL::NFT + (b == 0 ? BX : 0);
         for (int k = tid; k < nf; k += NT) {
             pair_t<T> F2o[6];
-            if (k < L::NFX) tile_face<T, 0, UNI>(I, S, k % (BX + 1) - 1, k / (BX + 1), F2o);
-            else if (k < SL::NFT) tile_face<T, 1, UNI>(I, S, (k - L::NFX) % BX, (k - L::NFX) / BX, F2o);
-            else tile_face<T, 1, UNI>(I, S, k - SL::NFT, -1, F2o);
+            if (k < SL::NXI) {
+                const int xa = k % SL::XP - 1;
+                if (xa >= BX) continue;                   // the idle item of an x-face row
+                tile_face<T, 0, UNI>(I, S, xa, k / SL::XP, F2o);
+            } else if (k < SL::Y0) {
+                continue;
+            } else if (k < SL::NFT) {
+                tile_face<T, 1, UNI>(I, S, (k - SL::Y0) % BX, (k - SL::Y0) / BX, F2o);
+            } else {
+                tile_face<T, 1, UNI>(I, S, k - SL::NFT, -1, F2o);
+            }
             pair_t<T> *dst = k < SL::NFT ? flux + k : keep0 + (k - SL::NFT);   // block 0: buffer 0
             const int stride = k < SL::NFT ? SL::NFT : BX;
 #pragma unroll
@@ -378,8 +395,8 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
             pair_t<T> J[Q];
 #pragma unroll
             for (int q = 0; q < Q; q++) J[q] = pr(T(0));
-            const int kw = y * (BX + 1) + x, ke = kw + 1;
-            const int kn = L::NFX + y * BX + x;               // face between rows y and y + 1
+            const int kw = y * SL::XP + x, ke = kw + 1;       // faces x - 1 | x and x | x + 1
+            const int kn = SL::Y0 + y * BX + x;               // face between rows y and y + 1
 #pragma unroll
             for (int m = 0; m < 6; m++) {
                 const int qx = xset(m), qy = yset(m);
@@ -448,7 +465,7 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
                               sizeof(T) * 2 * L::W1 % 16 == 0 && sizeof(T) * L::A1 % 16 == 0 &&
                               sizeof(T) * BY * L::W3 % 16 == 0 && sizeof(T) * BY * L::W2 % 16 == 0 &&
                               sizeof(T) * BY * L::W1 % 16 == 0 && sizeof(pair_t<T>) * SL::NFT % 16 == 0 &&
-                              sizeof(pair_t<T>) * (L::NFX + (BY - 1) * BX) % 16 == 0,
+                              sizeof(pair_t<T>) * (SL::Y0 + (BY - 1) * BX) % 16 == 0,
                           "16-byte ring rows");
             constexpr int NPHI = PHB, NMU = NPHI + MUB, NP = NMU + PB, NAUX = NP + 7 * AB;
             constexpr int NALL = NAUX + Q * BB;
