@@ -37,7 +37,14 @@ struct FusedLayout {
     static constexpr int W3 = BX + 6, H3 = BY + 6, A3 = W3 * H3;
     static constexpr int W4 = BX + 8, H4 = BY + 8, A4 = W4 * H4;
     static constexpr int NG = W4 + H4;                       // geometry entries (x then y)
-    static constexpr int NFX = (BX + 1) * BY, NFY = BX * (BY + 1), NFT = NFX + NFY;
+    static constexpr int NFX = (BX + 1) * BY, NFY = BX * (BY + 1);
+    // face items, in the order the threads take them and the flux buffer
+    // stores them: the x faces on the pitch of the R1 planes (XP items a row,
+    // the last one idle), so that a warp's faces read consecutive R1 entries
+    // across a row change; then, from item Y0 (a whole number of warps), the
+    // y faces one row of BX per warp.  Either way no warp reads two R1
+    // entries of one shared-memory bank.
+    static constexpr int XP = W1, NXI = XP * BY, Y0 = (NXI + 31) / 32 * 32, NFT = Y0 + NFY;
     static constexpr int NR1 = 7 + 18;                       // R1 planes
     static constexpr size_t al(size_t v) { return (v + 15) / 16 * 16; }
     static constexpr size_t o_geo = 0;                       // 11 T arrays + 2 int arrays of NG
@@ -93,7 +100,7 @@ struct Tile {
     T *ga;          // [11][NG] geometry coefficients, positions x -4..BX+3 then y -4..BY+3
     int *gg, *gf;   // [NG] global index (-1 outside), flags: 1 om=-1, 2 op=+1, 4 lo wall, 8 hi wall
     phi_t<T> *phi;  // R4
-    pair_t<T> *flux;  // [6][NFT] (f, g) flux pairs; unless SEP, aliases sf and sg (dead once phase 4 ends)
+    pair_t<T> *flux;  // [6][NFT] (f, g) flux pairs by face item; unless SEP, aliases sf and sg (dead once phase 4 ends)
     T *mu;          // R3
     T *p;           // R2
     T *gmx, *gmy, *lmu, *gfx, *gfy, *gpx, *gpy;  // R1
@@ -559,11 +566,18 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const InstDev *__restrict__ i
     const bool own = tid < BX * BY && gi < I.nx && gj < I.ny;
     const long long c = own ? cell(gi, gj) : 0;
 
-    // ---- phase 5: every face of the tile once (x faces first in the index space)
+    // ---- phase 5: every face of the tile once (x faces first in the item space)
     for (int k = tid; k < L::NFT; k += NT) {
         pair_t<T> F2o[6];
-        if (k < L::NFX) tile_face<T, 0, UNI>(I, S, k % (BX + 1) - 1, k / (BX + 1), F2o);
-        else tile_face<T, 1, UNI>(I, S, (k - L::NFX) % BX, (k - L::NFX) / BX - 1, F2o);
+        if (k < L::NXI) {
+            const int xa = k % L::XP - 1;
+            if (xa >= BX) continue;                       // the idle item of an x-face row
+            tile_face<T, 0, UNI>(I, S, xa, k / L::XP, F2o);
+        } else if (k < L::Y0) {
+            continue;
+        } else {
+            tile_face<T, 1, UNI>(I, S, (k - L::Y0) % BX, (k - L::Y0) / BX - 1, F2o);
+        }
 #pragma unroll
         for (int m = 0; m < 6; m++) S.flux[m * L::NFT + k] = F2o[m];
     }
@@ -576,8 +590,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const InstDev *__restrict__ i
 #pragma unroll
     for (int q = 0; q < Q; q++) J[q] = pr(T(0));
     {
-        const int kw = y * (BX + 1) + x, ke = kw + 1;                 // west and east faces
-        const int ks = L::NFX + y * BX + x, kn = ks + BX;            // south and north faces
+        const int kw = y * L::XP + x, ke = kw + 1;                    // west and east faces
+        const int ks = L::Y0 + y * BX + x, kn = ks + BX;             // south and north faces
 #pragma unroll
         for (int m = 0; m < 6; m++) {
             const int qx = xset(m), qy = yset(m);
