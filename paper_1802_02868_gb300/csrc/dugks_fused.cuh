@@ -152,6 +152,22 @@ struct Tile {
     __device__ __forceinline__ T c(int k, int axis, int pos) const { return ga[k * L::NG + ge(axis, UNI ? 0 : pos)]; }
     // index step from row y to row y + d of the R1 planes
     __device__ __forceinline__ int rs1(int y, int d) const { return d * L::W1; }
+    // position of item r of a phase over the H rows of a ring of radius R
+    // (width BX + 2R) starting at row y0: the first H * BX items one row of BX
+    // (a warp) each, then the 2R right-hand columns of every row, so that a
+    // warp reads one row of every ring and no two of its lanes hit one
+    // shared-memory bank
+    static __device__ __forceinline__ void ring_item(int r, int H, int R, int y0, int &x, int &y)
+    {
+        if (r < H * BX) {
+            x = r % BX - R;
+            y = y0 + r / BX;
+        } else {
+            const int k = r - H * BX;
+            x = BX - R + k % (2 * R);
+            y = y0 + k / (2 * R);
+        }
+    }
 };
 
 // Face macroscopic variables from the nine bar distributions of each kind at
@@ -435,7 +451,8 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const InstDev *__restrict__ i
 
     // ---- phase 2: mu on R3 (Eq. chemicalpotential), differences of the stored phi
     for (int r = tid; r < L::A3; r += NT) {
-        const int x = r % L::W3 - 3, y = r / L::W3 - 3;
+        int x, y;
+        TL::ring_item(r, L::H3, 3, -3, x, y);
         T mu = 0;
         if (S.ok(0, x) && S.ok(1, y)) {
             const phi_t<T> p0 = S.phi[TL::i4(x, y)];
@@ -448,7 +465,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const InstDev *__restrict__ i
                          * phi_subc(p0, I.cM);
             mu = dpsi - Pr.kappa * lap;
         }
-        S.mu[r] = mu;
+        S.mu[TL::i3(x, y)] = mu;
     }
     cp_wait<0>();   // tilde f and g have landed
     __syncthreads();
@@ -457,7 +474,9 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const InstDev *__restrict__ i
     const T cs2 = Cst<T>::cs2;
     // ---- phase 3: p on R2 (Eqs. u, P); needs grad mu, lap mu, grad phi and f~
     for (int r = tid; r < L::A2; r += NT) {
-        const int x = r % L::W2 - 2, y = r / L::W2 - 2;
+        int x, y;
+        TL::ring_item(r, L::H2, 2, -2, x, y);
+        const int k2 = TL::i2(x, y);
         T vp = 0;
         if (S.ok(0, x) && S.ok(1, y)) {
             const T m0 = S.mu[TL::i3(x, y)];
@@ -478,7 +497,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const InstDev *__restrict__ i
             T sf = 0, mx = 0, my = 0;
 #pragma unroll
             for (int q = 0; q < Q; q++) {
-                const T v = S.sf[q * L::A2 + r];
+                const T v = S.sf[q * L::A2 + k2];
                 sf += v;
                 if (cx(q)) mx += T(cx(q)) * v;
                 if (cy(q)) my += T(cy(q)) * v;
@@ -488,7 +507,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const InstDev *__restrict__ i
             const T uy = (T(3) * my + hdt * Fy) * irho;
             vp = sf + hdt * cs2 * (ux * Pr.drho * gfx + uy * Pr.drho * gfy - Pr.gamma * rho * Pr.lambda * lmu);
         }
-        S.p[r] = vp;
+        S.p[k2] = vp;
     }
     __syncthreads();
 
@@ -496,11 +515,13 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const InstDev *__restrict__ i
     const T dt = Pr.dt;
     const T ag = Pr.gca, bg = Pr.gcb, cg = Pr.gcc;
     for (int r = tid; r < L::A1; r += NT) {
-        const int x = r % L::W1 - 1, y = r / L::W1 - 1;
+        int x, y;
+        TL::ring_item(r, L::H1, 1, -1, x, y);
+        const int k1 = TL::i1(x, y);
         if (!S.ok(0, x) || !S.ok(1, y)) {
-            S.gmx[r] = 0; S.gmy[r] = 0; S.lmu[r] = 0; S.gfx[r] = 0; S.gfy[r] = 0; S.gpx[r] = 0; S.gpy[r] = 0;
+            S.gmx[k1] = 0; S.gmy[k1] = 0; S.lmu[k1] = 0; S.gfx[k1] = 0; S.gfy[k1] = 0; S.gpx[k1] = 0; S.gpy[k1] = 0;
 #pragma unroll
-            for (int q = 0; q < Q; q++) S.bp[q * L::A1 + r] = pr(T(0));
+            for (int q = 0; q < Q; q++) S.bp[q * L::A1 + k1] = pr(T(0));
             continue;
         }
         const int k2 = TL::i2(x, y);
@@ -518,7 +539,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const InstDev *__restrict__ i
                     + S.c(1, 0, x) * phi_sub(S.phi[TL::i4(x + S.op(0, x), y)], ph0);
         const T gfy = S.c(0, 1, y) * phi_sub(S.phi[TL::i4(x, y + S.om(1, y))], ph0)
                     + S.c(1, 1, y) * phi_sub(S.phi[TL::i4(x, y + S.op(1, y))], ph0);
-        S.gmx[r] = gmx; S.gmy[r] = gmy; S.lmu[r] = lmu; S.gfx[r] = gfx; S.gfy[r] = gfy; S.gpx[r] = gpx; S.gpy[r] = gpy;
+        S.gmx[k1] = gmx; S.gmy[k1] = gmy; S.lmu[k1] = lmu; S.gfx[k1] = gfx; S.gfy[k1] = gfy; S.gpx[k1] = gpx; S.gpy[k1] = gpy;
         T fv[Q];
         T mx = 0, my = 0;
 #pragma unroll
@@ -554,7 +575,7 @@ __global__ void __launch_bounds__(NT, MINB) k_step(const InstDev *__restrict__ i
 #pragma unroll
             for (int e = 0; e < (k == 0 ? 1 : 2); e++) {
                 const int qq = e == 0 ? q : opp(q);
-                S.bp[qq * L::A1 + r] = pfma(pr(af, ag), pr(fv[qq], S.sg[qq * L::A1 + r]),
+                S.bp[qq * L::A1 + k1] = pfma(pr(af, ag), pr(fv[qq], S.sg[qq * L::A1 + k1]),
                                             pfma(pr(bf, bg), pr(feq[e], geq[e]), pmul(pr(cf, cg), pr(Ff[e], Fg[e]))));
             }
         }

@@ -206,26 +206,11 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
         __syncthreads();
     };
 
-    // item r of a ring phase of radius R over rows [y0, y0 + n): the first
-    // n * BX items one row of BX (a warp) each, then the 2R right-hand
-    // columns of every row, so that a warp reads one row of every ring and
-    // no two of its lanes hit one shared-memory bank
-    auto ring_item = [&](int r, int n, int R, int y0, int &x, int &y) {
-        if (r < n * BX) {
-            x = r % BX - R;
-            y = y0 + r / BX;
-        } else {
-            const int k = r - n * BX;
-            x = BX - R + k % (2 * R);
-            y = y0 + k / (2 * R);
-        }
-    };
-
     // mu on R3 rows [y0, y1) (Eq. chemicalpotential)
     auto mu_rows = [&](int y0, int y1) {
         for (int r = tid; r < (y1 - y0) * L::W3; r += NT) {
             int x, y;
-            ring_item(r, y1 - y0, 3, y0, x, y);
+            TL::ring_item(r, y1 - y0, 3, y0, x, y);
             T mu = 0;
             if (S.ok(0, x) && S.ok(1, y)) {
                 const phi_t<T> p0 = S.phi[TL::i4(x, y)];
@@ -245,7 +230,7 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
     auto p_rows = [&](int y0, int y1, int fr0) {
         for (int r = tid; r < (y1 - y0) * L::W2; r += NT) {
             int x, y;
-            ring_item(r, y1 - y0, 2, y0, x, y);
+            TL::ring_item(r, y1 - y0, 2, y0, x, y);
             T vp = 0;
             if (S.ok(0, x) && S.ok(1, y)) {
                 const T m0 = S.mu[TL::i3(x, y)];
@@ -287,7 +272,7 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
     auto r1_rows = [&](int y0, int y1, int fr0, int gr0) {
         for (int r = tid; r < (y1 - y0) * L::W1; r += NT) {
             int x, y;
-            ring_item(r, y1 - y0, 1, y0, x, y);
+            TL::ring_item(r, y1 - y0, 1, y0, x, y);
             const int k1 = TL::i1(x, y);
             if (!S.ok(0, x) || !S.ok(1, y)) {
                 S.gmx[k1] = 0; S.gmy[k1] = 0; S.lmu[k1] = 0; S.gfx[k1] = 0; S.gfy[k1] = 0; S.gpx[k1] = 0; S.gpy[k1] = 0;
