@@ -41,8 +41,11 @@ struct StripLayout {
     static constexpr int FROWS = BY + 1, GROWS = BY;      // staged tilde rows of a block (f: 1..BY+1, g: 1..BY)
     static constexpr size_t al(size_t v) { return (v + 15) / 16 * 16; }
     static constexpr size_t o_un = L::o_un;               // after the R1 planes
-    static constexpr size_t st_f = sizeof(T) * Q * FROWS * L::W2;
-    static constexpr size_t st_g = sizeof(T) * Q * GROWS * L::W1;
+    // staging rows on pitch SP with column x at SO + x: x = 0 on a 16-byte
+    // boundary, so that a uniform row can arrive in 16-byte copies
+    static constexpr int SP = BX + 8, SO = 4;
+    static constexpr size_t st_f = sizeof(T) * Q * FROWS * SP;
+    static constexpr size_t st_g = sizeof(T) * Q * GROWS * SP;
     static constexpr size_t st_flux = sizeof(pair_t<T>) * 6 * NFT;
     static constexpr size_t un = (st_f + st_g > st_flux) ? st_f + st_g : st_flux;
     static constexpr size_t o_st = o_un;                  // staging: the flux bytes, free after the update
@@ -61,8 +64,8 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
     using TL = Tile<T, BX, BY, UNI, false>;
     extern __shared__ __align__(16) unsigned char smem[];
     TL S(smem);
-    T *stf = (T *)(smem + SL::o_st);                      // staged tilde f [Q][FROWS][W2]
-    T *stg = stf + Q * SL::FROWS * L::W2;                 // staged tilde g [Q][GROWS][W1]
+    T *stf = (T *)(smem + SL::o_st);                      // staged tilde f [Q][FROWS][SP]
+    T *stg = stf + Q * SL::FROWS * SL::SP;                // staged tilde g [Q][GROWS][SP]
     phi_t<T> *phst = (phi_t<T> *)(smem + SL::o_phst);    // staged phi rows 4 .. BY + 3 of the next block
     pair_t<T> *flux = (pair_t<T> *)(smem + SL::o_un);    // [6][NFT], by face item
     // two [6][BX] buffers: block b reads its bottom y faces from buffer b % 2
@@ -95,6 +98,12 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
     }
     const T cs2 = Cst<T>::cs2;
     const T hdt = T(0.5) * Pr.dt, dt = Pr.dt;
+    // 16-byte staging copies: FP32, uniform periodic, a width that is a
+    // multiple of 4 (row pitches and instance offsets are multiples of 32)
+    // and 16-byte aligned planes
+    const bool wide = UNI && sizeof(T) == 4 && I.nx % 4 == 0 &&
+                      ((reinterpret_cast<unsigned long long>(io.f_in) | reinterpret_cast<unsigned long long>(io.g_in) |
+                        (unsigned long long)(N * sizeof(T))) & 15) == 0;
     const T ag = Pr.gca, bg = Pr.gcb, cg = Pr.gcc;
     // global index of a column (x) or of row y of block b (wrapped on a periodic
     // axis, -1 outside the domain)
@@ -173,30 +182,63 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
     // staging area (zero outside the domain)
     auto load_fg = [&](int b, int fr0, int fr1, int gr0, int gr1) {
         const int bb = b < 0 ? 0 : b;
+        if (wide) {
+            // per row ten copies of each plane: the 32 interior columns in
+            // 16-byte pieces of four, and the halo (f: x = -2..-1 and 32..33 in
+            // 8-byte pairs; g: x = -1 and 32).  A piece never straddles the
+            // periodic wrap: the width and the strip origin are multiples of 4.
+            for (int r = tid; r < (fr1 - fr0) * 10; r += NT) {
+                const int yy = r / 10, k = r % 10;
+                const int x = k < 8 ? 4 * k : k == 8 ? -2 : BX;
+                const long long c = cell(S.gidx(0, x), grow(bb, fr0 + yy));
+                T *d = stf + yy * SL::SP + (x + SL::SO);
+                if (k < 8) {
+#pragma unroll
+                    for (int q = 0; q < Q; q++) cp_async<16>(d + q * SL::FROWS * SL::SP, io.f_in + q * N + c);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < Q; q++) cp_async<8>(d + q * SL::FROWS * SL::SP, io.f_in + q * N + c);
+                }
+            }
+            for (int r = tid; r < (gr1 - gr0) * 10; r += NT) {
+                const int yy = r / 10, k = r % 10;
+                const int x = k < 8 ? 4 * k : k == 8 ? -1 : BX;
+                const long long c = cell(S.gidx(0, x), grow(bb, gr0 + yy));
+                T *d = stg + yy * SL::SP + (x + SL::SO);
+                if (k < 8) {
+#pragma unroll
+                    for (int q = 0; q < Q; q++) cp_async<16>(d + q * SL::GROWS * SL::SP, io.g_in + q * N + c);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < Q; q++) cp_async<4>(d + q * SL::GROWS * SL::SP, io.g_in + q * N + c);
+                }
+            }
+            return;
+        }
         for (int r = tid; r < (fr1 - fr0) * L::W2; r += NT) {
             const int x = r % L::W2 - 2, yy = r / L::W2;
             const int gi = S.gidx(0, x), gj = grow(bb, fr0 + yy);
-            T *d = stf + yy * L::W2 + (x + 2);
+            T *d = stf + yy * SL::SP + (x + SL::SO);
             if (UNI || (gi >= 0 && gj >= 0)) {
                 const long long c = cell(gi, gj);
 #pragma unroll
-                for (int q = 0; q < Q; q++) cp_async<sizeof(T)>(d + q * SL::FROWS * L::W2, io.f_in + q * N + c);
+                for (int q = 0; q < Q; q++) cp_async<sizeof(T)>(d + q * SL::FROWS * SL::SP, io.f_in + q * N + c);
             } else {
 #pragma unroll
-                for (int q = 0; q < Q; q++) d[q * SL::FROWS * L::W2] = T(0);
+                for (int q = 0; q < Q; q++) d[q * SL::FROWS * SL::SP] = T(0);
             }
         }
         for (int r = tid; r < (gr1 - gr0) * L::W1; r += NT) {
             const int x = r % L::W1 - 1, yy = r / L::W1;
             const int gi = S.gidx(0, x), gj = grow(bb, gr0 + yy);
-            T *d = stg + yy * L::W1 + (x + 1);
+            T *d = stg + yy * SL::SP + (x + SL::SO);
             if (UNI || (gi >= 0 && gj >= 0)) {
                 const long long c = cell(gi, gj);
 #pragma unroll
-                for (int q = 0; q < Q; q++) cp_async<sizeof(T)>(d + q * SL::GROWS * L::W1, io.g_in + q * N + c);
+                for (int q = 0; q < Q; q++) cp_async<sizeof(T)>(d + q * SL::GROWS * SL::SP, io.g_in + q * N + c);
             } else {
 #pragma unroll
-                for (int q = 0; q < Q; q++) d[q * SL::GROWS * L::W1] = T(0);
+                for (int q = 0; q < Q; q++) d[q * SL::GROWS * SL::SP] = T(0);
             }
         }
     };
@@ -248,11 +290,11 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
                 const T rho = rho_of<T>(I, phi);
                 const T Fx = -phi * gmx + (rho - Pr.rho_ref) * Pr.gxa;
                 const T Fy = -phi * gmy + (rho - Pr.rho_ref) * Pr.gya;
-                const T *fr = stf + (y - fr0) * L::W2 + (x + 2);
+                const T *fr = stf + (y - fr0) * SL::SP + (x + SL::SO);
                 T sf = 0, mx = 0, my = 0;
 #pragma unroll
                 for (int q = 0; q < Q; q++) {
-                    const T v = fr[q * SL::FROWS * L::W2];
+                    const T v = fr[q * SL::FROWS * SL::SP];
                     sf += v;
                     if (cx(q)) mx += T(cx(q)) * v;
                     if (cy(q)) my += T(cy(q)) * v;
@@ -295,13 +337,13 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
             const T gfy = S.c(0, 1, y) * phi_sub(S.phi[TL::i4(x, y + S.om(1, y))], ph0)
                         + S.c(1, 1, y) * phi_sub(S.phi[TL::i4(x, y + S.op(1, y))], ph0);
             S.gmx[k1] = gmx; S.gmy[k1] = gmy; S.lmu[k1] = lmu; S.gfx[k1] = gfx; S.gfy[k1] = gfy; S.gpx[k1] = gpx; S.gpy[k1] = gpy;
-            const T *fr = stf + (y - fr0) * L::W2 + (x + 2);
-            const T *gr = stg + (y - gr0) * L::W1 + (x + 1);
+            const T *fr = stf + (y - fr0) * SL::SP + (x + SL::SO);
+            const T *gr = stg + (y - gr0) * SL::SP + (x + SL::SO);
             T fv[Q];
             T mx = 0, my = 0;
 #pragma unroll
             for (int q = 0; q < Q; q++) {
-                fv[q] = fr[q * SL::FROWS * L::W2];
+                fv[q] = fr[q * SL::FROWS * SL::SP];
                 if (cx(q)) mx += T(cx(q)) * fv[q];
                 if (cy(q)) my += T(cy(q)) * fv[q];
             }
@@ -332,7 +374,7 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
 #pragma unroll
                 for (int e = 0; e < (k == 0 ? 1 : 2); e++) {
                     const int qq = e == 0 ? q : opp(q);
-                    S.bp[qq * L::A1 + k1] = pfma(pr(af, ag), pr(fv[qq], gr[qq * SL::GROWS * L::W1]),
+                    S.bp[qq * L::A1 + k1] = pfma(pr(af, ag), pr(fv[qq], gr[qq * SL::GROWS * SL::SP]),
                                                  pfma(pr(bf, bg), pr(feq[e], geq[e]), pmul(pr(cf, cg), pr(Ff[e], Fg[e]))));
                 }
             }
