@@ -249,8 +249,11 @@ def test_every_shape_is_bit_identical_on_uniform_periodic_meshes(prec):
     """On uniform periodic meshes the strips (which prefetch the next block's
     rows and refill the shifted rings) and every tile shape execute the same
     arithmetic per cell: after 20 steps of a batch of uneven sizes, every shape
-    holds the same bits."""
-    cases = [I.stationary_drop(n=96, radius=24.0), I.stationary_drop(n=160, radius=40.0), I.roofline_drop(64)]
+    holds the same bits.  The widths cover the strip's staging copies: 16-byte
+    pieces on widths that are multiples of 32, and of 4 only (100: the last
+    strip's pieces wrap at the periodic edge), cell by cell otherwise (66)."""
+    cases = [I.stationary_drop(n=96, radius=24.0), I.stationary_drop(n=160, radius=40.0), I.roofline_drop(64),
+             I.stationary_drop(n=100, radius=25.0), I.stationary_drop(n=66, radius=16.0)]
     ref = None
     for k in range(dugks.NUM_TILE_SHAPES):
         s = dugks.Sim([c.mesh for c in cases], [c.params for c in cases], prec)
