@@ -179,7 +179,8 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
         }
     };
     // tilde f rows [fr0, fr1) and tilde g rows [gr0, gr1) of block b into the
-    // staging area (zero outside the domain)
+    // staging area (zero outside the domain); the f copies are committed as a
+    // group, the g copies are left for the caller to commit
     auto load_fg = [&](int b, int fr0, int fr1, int gr0, int gr1) {
         const int bb = b < 0 ? 0 : b;
         if (wide) {
@@ -200,6 +201,7 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
                     for (int q = 0; q < Q; q++) cp_async<8>(d + q * SL::FROWS * SL::SP, io.f_in + q * N + c);
                 }
             }
+            cp_commit();   // f and g in groups of their own: p waits for f only
             for (int r = tid; r < (gr1 - gr0) * 10; r += NT) {
                 const int yy = r / 10, k = r % 10;
                 const int x = k < 8 ? 4 * k : k == 8 ? -1 : BX;
@@ -228,6 +230,7 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
                 for (int q = 0; q < Q; q++) d[q * SL::FROWS * SL::SP] = T(0);
             }
         }
+        cp_commit();   // f and g in groups of their own: p waits for f only
         for (int r = tid; r < (gr1 - gr0) * L::W1; r += NT) {
             const int x = r % L::W1 - 1, yy = r / L::W1;
             const int gi = S.gidx(0, x), gj = grow(bb, gr0 + yy);
@@ -265,6 +268,7 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
             }
             S.mu[TL::i3(x, y)] = mu;
         }
+        cp_wait<1>();   // the block's tilde f rows (issued during the shift) are in
         __syncthreads();
     };
 
@@ -306,6 +310,7 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
             }
             S.p[TL::i2(x, y)] = vp;
         }
+        cp_wait<0>();   // and the tilde g rows
         __syncthreads();
     };
 
@@ -552,7 +557,7 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
             // the same thread then writes the geometry of the next block's new row r
             set_geo(L::W4 + 8 + r, false, 4 + r, grow(b + 1, 4 + r));
         }
-        cp_wait<0>();   // the next block's tilde rows are in
+        // the next block's tilde rows land during its mu (f) and p (g) phases
         __syncthreads();
     }
 }
