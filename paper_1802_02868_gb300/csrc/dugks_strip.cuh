@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
     const bool wide = UNI && sizeof(T) == 4 && I.nx % 4 == 0 &&
                       ((reinterpret_cast<unsigned long long>(io.f_in) | reinterpret_cast<unsigned long long>(io.g_in) |
                         (unsigned long long)(N * sizeof(T))) & 15) == 0;
+    const bool wide_phi = wide && (reinterpret_cast<unsigned long long>(io.phi_in) & 15) == 0;
     const T ag = Pr.gca, bg = Pr.gcb, cg = Pr.gcc;
     // global index of a column (x) or of row y of block b (wrapped on a periodic
     // axis, -1 outside the domain)
@@ -166,6 +167,15 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
     };
     // the new phi rows 4 .. BY + 3 of block b into the phi staging rows
     auto load_phi_next = [&](int b) {
+        if (wide_phi) {
+            // two cells per 16-byte copy: x even and an even width, so a pair
+            // never straddles the periodic wrap
+            for (int r = tid; r < BY * (L::W4 / 2); r += NT) {
+                const int x = 2 * (r % (L::W4 / 2)) - 4, y = 4 + r / (L::W4 / 2);
+                cp_async<16>(phst + (y - 4) * L::W4 + (x + 4), io.phi_in + cell(S.gidx(0, x), grow(b, y)));
+            }
+            return;
+        }
         for (int r = tid; r < BY * L::W4; r += NT) {
             const int x = r % L::W4 - 4, y = 4 + r / L::W4;
             const int gi = S.gidx(0, x), gj = grow(b, y);
