@@ -18,6 +18,7 @@
 // state; k_diag_inst adds the tiles of each instance in tile order, so the
 // result does not depend on timing.
 #pragma once
+#include "dugks_fused.cuh"
 #include "dugks_kernels.cuh"
 
 namespace dugks {
@@ -105,6 +106,18 @@ __global__ void __launch_bounds__(TX *TY) k_diag_f(const InstDev *__restrict__ i
     };
     load_f(0);
     if (live) {
+        // the phi region in asynchronous copies, in flight while the geometry is staged
+        for (int r = tid; r < W2 * (rows + 4); r += TX * TY) {
+            const int gi = wrap(true, i0 + r % W2 - 2), gj = wrap(false, j0 + r / W2 - 2);
+            if (gi >= 0 && gj >= 0) {
+                cp_async<sizeof(phi_t<T>)>(sphi + r, P.phi + cell_of(I, gi, gj));
+            } else {
+                phi_t<T> v;
+                phi_from_zero(v);
+                sphi[r] = v;
+            }
+        }
+        cp_commit();
         for (int e = tid; e < W2 + rows + 4; e += TX * TY) {
             const bool isx = e < W2;
             const int g = wrap(isx, isx ? i0 + e - 2 : j0 + (e - W2) - 2);
@@ -122,13 +135,7 @@ __global__ void __launch_bounds__(TX *TY) k_diag_f(const InstDev *__restrict__ i
             smo[e] = (signed char)m;
             spo[e] = (signed char)pp;
         }
-        for (int r = tid; r < W2 * (rows + 4); r += TX * TY) {
-            const int gi = wrap(true, i0 + r % W2 - 2), gj = wrap(false, j0 + r / W2 - 2);
-            phi_t<T> v;
-            phi_from_zero(v);
-            if (gi >= 0 && gj >= 0) v = P.phi[cell_of(I, gi, gj)];
-            sphi[r] = v;
-        }
+        cp_wait<0>();
     }
     __syncthreads();
     // geometry accessors: column x (entry x + 2), row y (entry W2 + y + 2)
