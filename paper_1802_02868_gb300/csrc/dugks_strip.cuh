@@ -405,6 +405,49 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
     p_rows(-2, 2, -2);
     r1_rows(-1, 1, -2, -1);
 
+    // the ring shift: word k of the rows that move down by BY; the rows of a
+    // ring are contiguous and 16-byte aligned, so they move in 16-byte words
+    constexpr int PHB = (int)(sizeof(phi_t<T>) * 8 * L::W4 / 16);
+    constexpr int MUB = (int)(sizeof(T) * 6 * L::W3 / 16);
+    constexpr int PB = (int)(sizeof(T) * 4 * L::W2 / 16);
+    constexpr int AB = (int)(sizeof(T) * 2 * L::W1 / 16);               // one aux plane
+    constexpr int BB = (int)(sizeof(pair_t<T>) * 2 * L::W1 / 16);       // one bar-plus plane
+    static_assert(sizeof(pair_t<T>) * BX % 16 == 0 && sizeof(phi_t<T>) * 8 * L::W4 % 16 == 0 &&
+                      sizeof(T) * 6 * L::W3 % 16 == 0 && sizeof(T) * 4 * L::W2 % 16 == 0 &&
+                      sizeof(T) * 2 * L::W1 % 16 == 0 && sizeof(T) * L::A1 % 16 == 0 &&
+                      sizeof(T) * BY * L::W3 % 16 == 0 && sizeof(T) * BY * L::W2 % 16 == 0 &&
+                      sizeof(T) * BY * L::W1 % 16 == 0 && sizeof(pair_t<T>) * SL::NFT % 16 == 0 &&
+                      sizeof(pair_t<T>) * (SL::Y0 + (BY - 1) * BX) % 16 == 0,
+                  "16-byte ring rows");
+    constexpr int NPHI = PHB, NMU = NPHI + MUB, NP = NMU + PB, NAUX = NP + 7 * AB;
+    constexpr int NALL = NAUX + Q * BB;
+    auto shift_word = [&](int k) {
+        float4 *d;
+        const float4 *src;
+        if (k < NPHI) {
+            // the thread that moves a word down also refills it with the
+            // next block's staged row
+            float4 *up = (float4 *)(S.phi + BY * L::W4) + k;
+            ((float4 *)S.phi)[k] = *up;
+            *up = ((const float4 *)phst)[k];
+            return;
+        } else if (k < NMU) {
+            d = (float4 *)S.mu + (k - NPHI);
+            src = (const float4 *)(S.mu + BY * L::W3) + (k - NPHI);
+        } else if (k < NP) {
+            d = (float4 *)S.p + (k - NMU);
+            src = (const float4 *)(S.p + BY * L::W2) + (k - NMU);
+        } else if (k < NAUX) {
+            const int pl = (k - NP) / AB, w = (k - NP) % AB;
+            d = (float4 *)(S.gmx + pl * L::A1) + w;
+            src = (const float4 *)(S.gmx + pl * L::A1 + BY * L::W1) + w;
+        } else {
+            const int q = (k - NAUX) / BB, w = (k - NAUX) % BB;
+            d = (float4 *)(S.bp + q * L::A1) + w;
+            src = (const float4 *)(S.bp + q * L::A1 + BY * L::W1) + w;
+        }
+        *d = *src;
+    };
     const int x = tid % BX, y = tid / BX;
     for (int b = 0; b < nblk; b++) {
         // ---- the new rows of every region; those of a later block were
@@ -503,59 +546,29 @@ __global__ void __launch_bounds__(NT, MINB) k_strip(const InstDev *__restrict__ 
             }
             if (!finite) atomicOr(io.status + t.x, ST_NONFINITE);
         }
+        // the threads that the update leaves idle shift the mu, p and aux
+        // rings, which the update does not read
+        constexpr int IDLE = NT - BX * BY;
+        if constexpr (IDLE > 0) {
+            if (tid >= BX * BY && b + 1 < nblk)
+                for (int k = NPHI + (tid - BX * BY); k < NAUX; k += IDLE) shift_word(k);
+        }
         cp_wait<0>();   // the next block's phi rows are in; the barrier makes them visible
         __syncthreads();
         if (b + 1 == nblk) break;
         // ---- the next block's tilde rows into the staging bytes (free once the
         // update has read the fluxes); while they are in flight, shift the
-        // shared ring rows and their geometry down by BY (a uniform instance
-        // keeps its one row record) and write the new rows' phi and geometry.
-        // The rows of a ring are contiguous and 16-byte aligned, so they move
-        // in 16-byte words: one pass over all the segments.
+        // phi and bar-plus ring rows and the row geometry down by BY (a
+        // uniform instance keeps its one row record) and write the new rows'
+        // phi and geometry.
         load_fg(b + 1, 1, BY + 2, 1, BY + 1);
         cp_commit();
-        {
-            constexpr int PHB = (int)(sizeof(phi_t<T>) * 8 * L::W4 / 16);
-            constexpr int MUB = (int)(sizeof(T) * 6 * L::W3 / 16);
-            constexpr int PB = (int)(sizeof(T) * 4 * L::W2 / 16);
-            constexpr int AB = (int)(sizeof(T) * 2 * L::W1 / 16);               // one aux plane
-            constexpr int BB = (int)(sizeof(pair_t<T>) * 2 * L::W1 / 16);       // one bar-plus plane
-            static_assert(sizeof(pair_t<T>) * BX % 16 == 0 && sizeof(phi_t<T>) * 8 * L::W4 % 16 == 0 &&
-                              sizeof(T) * 6 * L::W3 % 16 == 0 && sizeof(T) * 4 * L::W2 % 16 == 0 &&
-                              sizeof(T) * 2 * L::W1 % 16 == 0 && sizeof(T) * L::A1 % 16 == 0 &&
-                              sizeof(T) * BY * L::W3 % 16 == 0 && sizeof(T) * BY * L::W2 % 16 == 0 &&
-                              sizeof(T) * BY * L::W1 % 16 == 0 && sizeof(pair_t<T>) * SL::NFT % 16 == 0 &&
-                              sizeof(pair_t<T>) * (SL::Y0 + (BY - 1) * BX) % 16 == 0,
-                          "16-byte ring rows");
-            constexpr int NPHI = PHB, NMU = NPHI + MUB, NP = NMU + PB, NAUX = NP + 7 * AB;
-            constexpr int NALL = NAUX + Q * BB;
-            for (int k = tid; k < NALL; k += NT) {
-                float4 *d;
-                const float4 *src;
-                if (k < NPHI) {
-                    // the thread that moves a word down also refills it with the
-                    // next block's staged row
-                    float4 *up = (float4 *)(S.phi + BY * L::W4) + k;
-                    ((float4 *)S.phi)[k] = *up;
-                    *up = ((const float4 *)phst)[k];
-                    continue;
-                } else if (k < NMU) {
-                    d = (float4 *)S.mu + (k - NPHI);
-                    src = (const float4 *)(S.mu + BY * L::W3) + (k - NPHI);
-                } else if (k < NP) {
-                    d = (float4 *)S.p + (k - NMU);
-                    src = (const float4 *)(S.p + BY * L::W2) + (k - NMU);
-                } else if (k < NAUX) {
-                    const int pl = (k - NP) / AB, w = (k - NP) % AB;
-                    d = (float4 *)(S.gmx + pl * L::A1) + w;
-                    src = (const float4 *)(S.gmx + pl * L::A1 + BY * L::W1) + w;
-                } else {
-                    const int q = (k - NAUX) / BB, w = (k - NAUX) % BB;
-                    d = (float4 *)(S.bp + q * L::A1) + w;
-                    src = (const float4 *)(S.bp + q * L::A1 + BY * L::W1) + w;
-                }
-                *d = *src;
-            }
+        // the phi and bar-plus rings (mu, p and the aux planes were shifted
+        // during the update by the threads it leaves idle, if any)
+        if constexpr (NT > BX * BY) {
+            for (int k = tid; k < NPHI + (NALL - NAUX); k += NT) shift_word(k < NPHI ? k : k + (NAUX - NPHI));
+        } else {
+            for (int k = tid; k < NALL; k += NT) shift_word(k);
         }
         for (int r = tid; r < 8; r += NT) {
             S.gg[L::W4 + r] = S.gg[L::W4 + BY + r];
