@@ -49,9 +49,9 @@ PEAK_FP64_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # tile shape, from ncu captures of a 2048 x 2048 periodic drop
 # (dram__bytes_read.sum + dram__bytes_write.sum over 4,194,304 cells); valid
 # only for the kernel sources they were taken on.
-TRAFFIC_SOURCES_SHA = "e142789325a5e269"
+TRAFFIC_SOURCES_SHA = "d64a9240f3552be2"
 TRAFFIC_BYTES_PER_CELL_FP32 = {
-    "32x8 strip16/288": (347.070976e6 + 297.004544e6) / 4194304,
+    "32x8 strip16/288": (346.862080e6 + 297.274112e6) / 4194304,
 }
 
 
