@@ -355,7 +355,8 @@ def main():
         sim.set_tile_shape(args.tile_shape)
         tuned = (args.tile_shape, dugks.tile_shape_name(args.tile_shape), None)
     else:
-        tuned = sim.autotune(steps=10) if not args.no_autotune else (0, dugks.tile_shape_name(0), None)
+        k0 = sim.tile_shape()[0]
+        tuned = sim.autotune(steps=10) if not args.no_autotune else (k0, dugks.tile_shape_name(k0), None)
     for _ in range(args.warmup):
         sim.step(1)
     torch.cuda.synchronize()

@@ -188,13 +188,17 @@ const char *dugks_kernel_name(int k);
 int dugks_kernel_bytes_per_cell(const dugks_sim *sim, int k, double *bytes);
 
 /* Shapes of the fused step.  Tiles, one tile of cells per thread block:
-   0 = 32x8 cells on 256 threads (the default), 1 = 32x4 on 128 threads,
+   0 = 32x8 cells on 256 threads, 1 = 32x4 on 128 threads,
    2 = 32x12 on 384 threads, 3 = 32x8 on 352 threads with the face fluxes in
    their own shared memory (two blocks per SM).  Strips, one thread block of
    288 threads marching up 32 columns in blocks of 32x8 cells (two blocks per
    SM): 4 = strips of 8 blocks, 5 = 16 blocks, 6 = 32 blocks.  Every shape
    computes the same scheme: on uniform periodic meshes the results agree bit
-   for bit, elsewhere to rounding.  dugks_autotune times every shape on the sim's current state for
+   for bit, elsewhere to rounding.  A new fused-step sim starts with shape 5
+   when its meshes give at least 3 strips of 16 blocks per resident strip slot
+   (2 per SM in FP32, 1 in FP64), else shape 4 when they give at least 2
+   strips of 8 blocks per slot, else shape 0; a sim on the four-kernel step
+   reports shape 0.  dugks_autotune times every shape on the sim's current state for
    `steps` steps each (CUDA events on the sim's stream), restores the state and
    the per-instance status after each trial, keeps the fastest shape and
    returns its index and time per step.  It allocates a temporary snapshot of

@@ -59,7 +59,7 @@ struct dugks_sim {
     bool fused = true;            // one-launch step (k_step) or the four-kernel step
     bool use_graph = true;        // replay multi-step calls from a captured two-step graph
     bool use_uni = true;          // uniform periodic instances take the specialised fused step
-    int shape = 0;                // tile shape of the fused step (index into kShapes)
+    int shape = 0;                // shape of the fused step (index into kShapes; see default_shape)
     int n_sm = 1;                 // multiprocessors of the device (sizes persistent grids)
     // device memory source, fixed at creation (dugks_set_allocator)
     dugks_alloc_fn alloc_fn = nullptr;
@@ -308,6 +308,28 @@ int prepare_strip()
         attr_set = true;
     }
     return DUGKS_OK;
+}
+
+// Shape a new sim's fused step starts with.  A strip holds its SM for nb
+// blocks, so strips pay only when there are several of them per resident slot
+// (n_sm x blocks per SM); below that the 32x8 tile, whose short blocks balance
+// across the SMs, is faster.  On GB300 (FP32) the tile was fastest up to
+// 1024x1024 and on the 256x1024 Rayleigh-Taylor mesh, the 8-block strip on a
+// 16-instance batch (608 strips for 304 slots), and the 16-block strip from
+// 2048x2048 (1024 strips) and the 64-instance batch on; the thresholds below
+// reproduce those choices, and dugks_autotune measures the rest.
+int default_shape(const dugks_sim *s)
+{
+    if (!s->fused) return 0;
+    const long long slots = (long long)s->n_sm * (s->prec == DUGKS_FP64 ? 1 : 2);
+    auto strips = [&](int nb) {
+        long long c = 0;
+        for (const InstDev &I : s->h_inst) c += (long long)((I.nx + 31) / 32) * ((I.ny + 8 * nb - 1) / (8 * nb));
+        return c;
+    };
+    if (strips(kShapes[5].nb) >= 3 * slots) return 5;
+    if (strips(kShapes[4].nb) >= 2 * slots) return 4;
+    return 0;
 }
 
 // fused-step tile table of shape k: the uniform periodic instances' tiles first
@@ -1013,6 +1035,7 @@ int dugks_batch_create(int n, const dugks_mesh *meshes, const dugks_params *para
     s->N = cell;
     s->n_dense = dense;
     s->n_tiles = (int)tiles.size();
+    s->shape = default_shape(s);
     const size_t esz = s->prec == DUGKS_FP64 ? sizeof(double) : sizeof(float);
     // the bar-plus planes exist only for the four-kernel step
     const size_t plane_elems = (size_t)((s->fused ? 2 : 4) * Q + kNumScalarPlanes) * (size_t)s->N;

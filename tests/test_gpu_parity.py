@@ -269,6 +269,29 @@ def test_every_shape_is_bit_identical_on_uniform_periodic_meshes(prec):
 
 
 @pytest.mark.parametrize("prec", [dugks.FP64, dugks.FP32])
+def test_default_shape_follows_the_strip_count(prec):
+    """A new sim starts with the 16-block strip when there are at least three
+    such strips per resident slot (2 per SM in FP32, 1 in FP64), else with the
+    8-block strip at two per slot, else with the 32x8 tile."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    slots = n_sm * (1 if prec == dugks.FP64 else 2)
+
+    def strips(cases, nb):
+        return sum(-(-c.mesh.nx // 32) * -(-c.mesh.ny // (8 * nb)) for c in cases)
+
+    seen = set()
+    for cases in ([I.stationary_drop(n=64, radius=16.0)], [I.rayleigh_taylor()],
+                  I.batched_ensemble(16), I.batched_ensemble(64)):
+        want = 5 if strips(cases, 16) >= 3 * slots else 4 if strips(cases, 8) >= 2 * slots else 0
+        s = dugks.Sim([c.mesh for c in cases], [c.params for c in cases], prec)
+        assert s.tile_shape()[0] == want, (len(cases), want)
+        s.close()
+        seen.add(want)
+    assert 0 in seen and len(seen) >= 2
+
+
+@pytest.mark.parametrize("prec", [dugks.FP64, dugks.FP32])
 def test_tile_shapes_agree_and_autotune_restores_state(prec):
     """Every tile shape of the fused step computes the same scheme; the autotuner
     leaves the state as it found it and keeps one of the shapes."""
