@@ -46,6 +46,7 @@ struct dugks_sim {
     InstDev *d_inst = nullptr;
     int4 *d_tiles = nullptr;
     int4 *d_strips8 = nullptr;    // strips of up to DIAG_SB tiles of one tile column (diagnostics)
+    int2 *d_strip_rng = nullptr;  // per instance: first strip, number of strips
     int n_strips8 = 0;
     AxisRec *d_geo = nullptr;
     void *d_geoT = nullptr;       // the same records in the arithmetic type of the sim
@@ -79,7 +80,7 @@ struct dugks_sim {
     double2 *d_sums = nullptr;
     double *d_stage = nullptr;    // dense FP64 staging [5][n_dense]
     double *d_init_in = nullptr;  // the last init inputs phi, ux, uy, p [4][n_dense] (for the adjoint)
-    DiagPart *d_diag_parts = nullptr;   // per tile (allocated by the first diagnostics call)
+    DiagPart *d_diag_parts = nullptr;   // per diagnostics strip (allocated by the first diagnostics call)
     DiagOut *d_diag_out = nullptr;      // per instance
     bool has_init = false;
     Planes<double> P64{};
@@ -598,17 +599,24 @@ int ensure_strips8(dugks_sim *s)
 {
     if (s->d_strips8) return DUGKS_OK;
     std::vector<int4> st;
+    std::vector<int2> rng;
     for (int i = 0; i < s->n_inst; i++) {
         const InstDev &I = s->h_inst[i];
         const int nty = (I.ny + TY - 1) / TY;
+        const int first = (int)st.size();
         for (int tx = 0; tx < I.nx; tx += TX)
             for (int ty = 0; ty < nty; ty += DIAG_SB) st.push_back(make_int4(i, tx, ty * TY, std::min(DIAG_SB, nty - ty)));
+        rng.push_back(make_int2(first, (int)st.size() - first));
     }
     cudaError_t e = dmalloc(s, (void **)&s->d_strips8, sizeof(int4) * st.size());
+    if (e == cudaSuccess) e = dmalloc(s, (void **)&s->d_strip_rng, sizeof(int2) * rng.size());
     if (e == cudaSuccess) e = cudaMemcpy(s->d_strips8, st.data(), sizeof(int4) * st.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(s->d_strip_rng, rng.data(), sizeof(int2) * rng.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         dfree(s, s->d_strips8);
+        dfree(s, s->d_strip_rng);
         s->d_strips8 = nullptr;
+        s->d_strip_rng = nullptr;
         return cuda_status(e);
     }
     s->n_strips8 = (int)st.size();
@@ -643,8 +651,10 @@ int do_reduce(dugks_sim *s)
 template <typename T>
 int do_diag(dugks_sim *s, double *p_dense)
 {
+    const int rc = ensure_strips8(s);
+    if (rc) return rc;
     if (!s->d_diag_parts) {
-        cudaError_t e = dmalloc(s, (void **)&s->d_diag_parts, sizeof(DiagPart) * s->n_tiles);
+        cudaError_t e = dmalloc(s, (void **)&s->d_diag_parts, sizeof(DiagPart) * s->n_strips8);
         if (e == cudaSuccess) e = dmalloc(s, (void **)&s->d_diag_out, sizeof(DiagOut) * s->n_inst);
         if (e != cudaSuccess) {
             dfree(s, s->d_diag_parts);
@@ -652,14 +662,12 @@ int do_diag(dugks_sim *s, double *p_dense)
             return cuda_status(e);
         }
     }
-    const int rc = ensure_strips8(s);
-    if (rc) return rc;
     Planes<T> &P = planes<T>(s);
     const dim3 blk(TX, TY);
     const unsigned g = (unsigned)s->n_strips8;
     { Timed t(s, K_DIAG); k_diag_f<T><<<g, blk, 0, s->stream>>>(s->d_inst, s->d_strips8, (const AxisRecT<T> *)s->d_geoT, s->d_geo, P,
                                                                   s->d_diag_parts, p_dense, s->d_dense0); }
-    { Timed t(s, -1); k_diag_inst<<<(unsigned)s->n_inst, DIAG_INST_THREADS, 0, s->stream>>>(s->d_inst, s->d_status, s->d_diag_parts, s->d_diag_out); }
+    { Timed t(s, -1); k_diag_inst<<<(unsigned)s->n_inst, DIAG_INST_THREADS, 0, s->stream>>>(s->d_strip_rng, s->d_status, s->d_diag_parts, s->d_diag_out); }
     return cuda_status(cudaGetLastError());
 }
 
@@ -692,6 +700,7 @@ void free_sim(dugks_sim *s)
     dfree(s, s->d_tiles);
     for (int k = 0; k < DUGKS_NUM_TILE_SHAPES; k++) dfree(s, s->d_tiles_s[k]);
     dfree(s, s->d_strips8);
+    dfree(s, s->d_strip_rng);
     dfree(s, s->d_geo);
     dfree(s, s->d_geoT);
     dfree(s, s->d_dense0);

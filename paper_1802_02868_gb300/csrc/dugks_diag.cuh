@@ -45,9 +45,11 @@ __device__ __forceinline__ double diag_nan() { return __longlong_as_double(0x7ff
 // walks the strip's tiles: for each cell grad mu, lap mu, grad phi, F, u and
 // p (Eqs. u, P) as k_mu and k_macro form them (in FP32 with the fast
 // division), the Laplace pressure and the region sums, with the next tile's
-// tilde f already in flight.  One
-// partial per tile (at its index in the tile table), so k_diag_inst adds
-// them in tile order as before.  Writes nothing else (and P if asked).
+// tilde f already in flight.  Each thread accumulates its cells' terms over
+// the strip in T; the block reduces them once (warp shuffles, then the warps
+// in order) into one partial per strip, at the strip's index, and
+// k_diag_inst adds an instance's strips in order.  Writes nothing else (and
+// P if asked).
 constexpr int DIAG_SB = 8;
 template <typename T>
 __global__ void __launch_bounds__(TX *TY) k_diag_f(const InstDev *__restrict__ insts, const int4 *__restrict__ strips,
@@ -63,9 +65,9 @@ __global__ void __launch_bounds__(TX *TY) k_diag_f(const InstDev *__restrict__ i
     __shared__ T sgeo[8][NE];
     __shared__ signed char smo[NE], spo[NE];
     __shared__ double syc[H2];                  // FP64 row centres, for the crossing heights
-    __shared__ T red[2][TX * TY / 32][DIAG_SUMS];
-    __shared__ unsigned long long s_front[SB], s_tip[SB];
-    __shared__ int s_ncross[SB];
+    __shared__ T red[TX * TY / 32][DIAG_SUMS];
+    __shared__ unsigned long long s_front, s_tip;
+    __shared__ int s_ncross;
     const int4 st = strips[blockIdx.x];
     const InstDev &I = insts[st.x];
     const ParT<T> &Pr = par<T>(I);
@@ -73,8 +75,6 @@ __global__ void __launch_bounds__(TX *TY) k_diag_f(const InstDev *__restrict__ i
     const int tid = threadIdx.y * TX + threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool live = !(P.status[st.x] & ST_NONFINITE);
     const long long N = P.N;
-    const int ntx = (I.nx + TX - 1) / TX;
-    const int tile_first = I.tile0 + (j0 / TY) * ntx + i0 / TX;   // the strip's tiles are tile_first + rb ntx
     const int rows = nb * TY;
     auto i2 = [](int x, int y) { return (y + 2) * W2 + (x + 2); };
     auto i1 = [](int x, int y) { return (y + 1) * W1 + (x + 1); };
@@ -87,10 +87,10 @@ __global__ void __launch_bounds__(TX *TY) k_diag_f(const InstDev *__restrict__ i
         }
         return (g < 0 || g >= n) ? -1 : g;
     };
-    if (tid < SB) {
-        s_front[tid] = 0ull;
-        s_tip[tid] = 0x7ff0000000000000ull;   // +inf
-        s_ncross[tid] = 0;
+    if (tid == 0) {
+        s_front = 0ull;
+        s_tip = 0x7ff0000000000000ull;   // +inf
+        s_ncross = 0;
     }
     const int x = threadIdx.x, y = threadIdx.y;
     const int i = i0 + x;
@@ -157,14 +157,14 @@ __global__ void __launch_bounds__(TX *TY) k_diag_f(const InstDev *__restrict__ i
         }
     }
     __syncthreads();
+    T v[DIAG_SUMS];   // the thread's sums over its cells of the strip
+#pragma unroll
+    for (int k = 0; k < DIAG_SUMS; k++) v[k] = T(0);
     for (int rb = 0; rb < nb; rb++) {
         T cur[Q];
 #pragma unroll
         for (int q = 0; q < Q; q++) cur[q] = fv[q];
         if (rb + 1 < nb) load_f(rb + 1);   // the next tile's tilde f is in flight while this tile runs
-        T v[DIAG_SUMS];
-#pragma unroll
-        for (int k = 0; k < DIAG_SUMS; k++) v[k] = T(0);
         const int yr = rb * TY + y, j = j0 + yr;
         if (live && i < I.nx && j < I.ny) {
             const T cs2 = Cst<T>::cs2;
@@ -206,67 +206,67 @@ __global__ void __launch_bounds__(TX *TY) k_diag_f(const InstDev *__restrict__ i
             const T inv = fdiv(T(1), Pr.phiA - Pr.phiB);
             const T cn = b * inv;
             if (cn > T(0.5)) {
-                v[0] = vol;
-                v[1] = vol * gx(7, x);
-                v[2] = vol * gy(7, yr);
-                v[3] = vol * ux;
-                v[4] = vol * uy;
+                v[0] += vol;
+                v[1] += vol * gx(7, x);
+                v[2] += vol * gy(7, yr);
+                v[3] += vol * ux;
+                v[4] += vol * uy;
             }
-            if (cn > T(0.9)) { v[5] = vol * Pv; v[6] = vol; }
-            if (cn < T(0.1)) { v[7] = vol * Pv; v[8] = vol; }
+            if (cn > T(0.9)) { v[5] += vol * Pv; v[6] += vol; }
+            if (cn < T(0.1)) { v[7] += vol * Pv; v[8] += vol; }
             if (j + 1 < I.ny && cn < T(0.5)) {
                 const T c1 = (T(phi_val(sphi[i2(x, yr + 1)])) - Pr.phiB) * inv;
                 if (c1 >= T(0.5)) {
                     const double y0 = syc[yr + 2], y1 = syc[yr + 3];
                     const double yy = y0 + (double)((T(0.5) - cn) / (c1 - cn)) * (y1 - y0);
                     const unsigned long long bits = (unsigned long long)__double_as_longlong(yy);
-                    atomicMax(&s_front[rb], bits);
-                    atomicMin(&s_tip[rb], bits);
-                    atomicAdd(&s_ncross[rb], 1);
+                    atomicMax(&s_front, bits);
+                    atomicMin(&s_tip, bits);
+                    atomicAdd(&s_ncross, 1);
                 }
             }
         }
-        // fixed-order reduction of the tile in T: warp shuffles, then the
-        // warps in order, and one conversion per tile (a warp-wide FP64
-        // instruction occupies GB300's FP64 pipe for 16 cycles even with one
-        // lane active); the shared slots alternate between tiles
+    }
+    // fixed-order reduction of the strip in T: warp shuffles, then the warps
+    // in order, and one conversion per strip (a warp-wide FP64 instruction
+    // occupies GB300's FP64 pipe for 16 cycles even with one lane active)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
+    for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-            for (int k = 0; k < DIAG_SUMS; k++) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-        }
-        if (lane == 0) {
+        for (int k = 0; k < DIAG_SUMS; k++) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    }
+    if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < DIAG_SUMS; k++) red[rb & 1][warp][k] = v[k];
+        for (int k = 0; k < DIAG_SUMS; k++) red[warp][k] = v[k];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        DiagPart out;
+        for (int k = 0; k < DIAG_SUMS; k++) {
+            T a = red[0][k];
+            for (int w = 1; w < TX * TY / 32; w++) a += red[w][k];
+            out.s[k] = (double)a;
         }
-        __syncthreads();
-        if (tid == 0) {
-            DiagPart out;
-            for (int k = 0; k < DIAG_SUMS; k++) {
-                T a = red[rb & 1][0][k];
-                for (int w = 1; w < TX * TY / 32; w++) a += red[rb & 1][w][k];
-                out.s[k] = (double)a;
-            }
-            out.front = s_ncross[rb] ? __longlong_as_double((long long)s_front[rb]) : -INFINITY;
-            out.tip = s_ncross[rb] ? __longlong_as_double((long long)s_tip[rb]) : INFINITY;
-            parts[tile_first + rb * ntx] = out;
-        }
+        out.front = s_ncross ? __longlong_as_double((long long)s_front) : -INFINITY;
+        out.tip = s_ncross ? __longlong_as_double((long long)s_tip) : INFINITY;
+        parts[blockIdx.x] = out;
     }
 }
 
-// One block per instance: its tiles' partials in tile order (a strided pass
-// per thread, then the threads in order), then the quotients.
+// One block per instance: its strips' partials in strip order (a strided
+// pass per thread, then the threads in order), then the quotients.  srng[k]
+// = (first strip, number of strips) of instance k.
 constexpr int DIAG_INST_THREADS = 128;
-__global__ void __launch_bounds__(DIAG_INST_THREADS) k_diag_inst(const InstDev *__restrict__ insts, const int *status,
+__global__ void __launch_bounds__(DIAG_INST_THREADS) k_diag_inst(const int2 *__restrict__ srng, const int *status,
                                                                  const DiagPart *__restrict__ parts, DiagOut *out)
 {
     __shared__ DiagPart red[DIAG_INST_THREADS];
-    const InstDev &I = insts[blockIdx.x];
+    const int2 R = srng[blockIdx.x];
     DiagPart a;
     for (int k = 0; k < DIAG_SUMS; k++) a.s[k] = 0.0;
     a.front = -INFINITY;
     a.tip = INFINITY;
-    for (int t = I.tile0 + threadIdx.x; t < I.tile0 + I.ntiles; t += DIAG_INST_THREADS) {
+    for (int t = R.x + threadIdx.x; t < R.x + R.y; t += DIAG_INST_THREADS) {
         const DiagPart &p = parts[t];
         for (int k = 0; k < DIAG_SUMS; k++) a.s[k] += p.s[k];
         a.front = fmax(a.front, p.front);

@@ -345,13 +345,21 @@ class Sim:
         _check("dugks_batch_step_each", load().dugks_batch_step_each(self.h, arr))
         return self
 
+    def diagnostics_array(self, out=None):
+        """dugks_diagnostics into an (instances, 9) float64 array (columns in
+        DIAG_FIELDS order, the layout of dugks_diag); `out` may be given."""
+        n = len(self.meshes)
+        if out is None:
+            out = np.empty((n, len(DIAG_FIELDS)))
+        if out.shape != (n, len(DIAG_FIELDS)) or out.dtype != np.float64 or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous float64 array of shape (%d, %d)" % (n, len(DIAG_FIELDS)))
+        _check("dugks_diagnostics", load().dugks_diagnostics(self.h, out.ctypes.data_as(ctypes.POINTER(Diag_t))))
+        return out
+
     def diagnostics(self):
         """Per-instance diagnostics (dugks_diagnostics) as dicts; one dict for a
         single instance."""
-        n = len(self.meshes)
-        out = (Diag_t * n)()
-        _check("dugks_diagnostics", load().dugks_diagnostics(self.h, out))
-        ds = [{k: getattr(d, k) for k in DIAG_FIELDS} for d in out]
+        ds = [dict(zip(DIAG_FIELDS, row)) for row in self.diagnostics_array().tolist()]
         return ds[0] if self.single else ds
 
     def laplace_pressure(self):

@@ -41,7 +41,10 @@ def _ambiguous_volume(mesh, phi, params, eps=1e-9):
 def _compare(dg, do, Pg, Po, mesh, m, params, rtol, ptol, eps=1e-9, ufloor=1e-16, mtol=0.0):
     """m: the oracle's moments; velocities are compared on the scale of the
     largest velocity of the mesh.  mtol: relative rounding of the volume sum
-    (FP32 sims sum single-precision cell volumes within a warp)."""
+    (FP32 sims sum single-precision cell volumes within a strip); in any
+    precision the two sides add the same FP64 volumes in different orders,
+    which moves an n-term sum by at most about n units of 2^-53 relative."""
+    mtol = max(mtol, mesh.ncells * 2.0 ** -53)
     assert abs(dg["mass"] - do["mass"]) <= _ambiguous_volume(mesh, m["phi"], params, eps) + mtol * do["mass"]
     scale_u = max(np.max(np.abs(m["ux"])), np.max(np.abs(m["uy"])), 1e-300)
     for k in KEYS[1:]:
