@@ -122,6 +122,23 @@ int dugks_moments(dugks_sim *sim, double *phi, double *rho, double *ux, double *
    arrays of n_instances doubles.  Synchronises. */
 int dugks_conservation(dugks_sim *sim, double *sum_phi, double *sum_rho);
 
+/* The sums of dugks_conservation without a synchronisation: enqueues the
+   reduction and its copy on the sim's stream and returns.  When the stream
+   has reached them, sums[2k] = sum |V| phi and sums[2k + 1] = sum |V| rho of
+   instance k (a host array of 2 n_instances doubles).  `sums` must be
+   page-locked (cudaHostAlloc or cudaHostRegister; pageable memory gives
+   DUGKS_ERR_ARG, since its copy could not be asynchronous) and must not be
+   read or freed before dugks_conservation_wait returns.  Steps enqueued
+   after the call run behind it on the stream, so a caller can enqueue step
+   k + 1 and then wait for the sums of step k while the GPU works. */
+int dugks_conservation_async(dugks_sim *sim, double *sums);
+
+/* Wait (on an event, not the whole stream) until the sums of the latest
+   dugks_conservation_async have landed; DUGKS_OK at once when none is
+   pending.  A single simulation whose state was non-finite at that point
+   returns DUGKS_ERR_NONFINITE, as dugks_conservation does. */
+int dugks_conservation_wait(dugks_sim *sim);
+
 /* Per-instance status (DUGKS_OK or DUGKS_ERR_NONFINITE) since creation or the
    last init; array of n_instances ints.  Synchronises. */
 int dugks_batch_status(dugks_sim *sim, int *per_instance_status);

@@ -89,6 +89,11 @@ struct dugks_sim {
     bool timing = false;
     std::vector<EventPair> ev_used;
     std::vector<cudaEvent_t> ev_pool;
+    // dugks_conservation_async: the event recorded after its copies, and a
+    // page-locked copy of the per-instance status taken with them
+    cudaEvent_t ev_cons = nullptr;
+    int *h_status = nullptr;
+    bool cons_pending = false;
     double k_ms[K_COUNT] = {0};
     long k_n[K_COUNT] = {0};
 };
@@ -721,6 +726,11 @@ void free_sim(dugks_sim *s)
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     for (auto &e : s->ev_used) { cudaEventDestroy(e.a); cudaEventDestroy(e.b); }
     for (auto e : s->ev_pool) cudaEventDestroy(e);
+    if (s->ev_cons) {
+        cudaEventSynchronize(s->ev_cons);
+        cudaEventDestroy(s->ev_cons);
+    }
+    if (s->h_status) cudaFreeHost(s->h_status);
     delete s;
 }
 
@@ -1257,6 +1267,36 @@ int dugks_conservation(dugks_sim *s, double *sum_phi, double *sum_rho)
         if (sum_rho) sum_rho[k] = h[k].y;
     }
     return sync_status(s);
+}
+
+int dugks_conservation_async(dugks_sim *s, double *sums)
+{
+    if (!s || !sums) return DUGKS_ERR_ARG;
+    if (!host_alias(sums)) return DUGKS_ERR_ARG;   // pageable memory: the copy could not be asynchronous
+    cudaError_t e = cudaSuccess;
+    if (!s->ev_cons) e = cudaEventCreateWithFlags(&s->ev_cons, cudaEventDisableTiming);
+    if (e == cudaSuccess && !s->h_status) e = cudaHostAlloc((void **)&s->h_status, sizeof(int) * s->n_inst, cudaHostAllocDefault);
+    if (e != cudaSuccess) return cuda_status(e);
+    int rc = s->prec == DUGKS_FP64 ? do_reduce<double>(s) : do_reduce<float>(s);
+    if (rc) return rc;
+    // d_sums holds (sum phi, sum rho) per instance: the layout of sums
+    e = cudaMemcpyAsync(sums, s->d_sums, sizeof(double2) * s->n_inst, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->h_status, s->d_status, sizeof(int) * s->n_inst, cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ev_cons, s->stream);
+    if (e != cudaSuccess) return cuda_status(e);
+    s->cons_pending = true;
+    return DUGKS_OK;
+}
+
+int dugks_conservation_wait(dugks_sim *s)
+{
+    if (!s) return DUGKS_ERR_ARG;
+    if (!s->cons_pending) return DUGKS_OK;
+    const cudaError_t e = cudaEventSynchronize(s->ev_cons);
+    if (e != cudaSuccess) return cuda_status(e);
+    s->cons_pending = false;
+    if (s->n_inst == 1 && (s->h_status[0] & ST_NONFINITE)) return DUGKS_ERR_NONFINITE;
+    return DUGKS_OK;
 }
 
 int dugks_batch_status(dugks_sim *s, int *per_instance_status)

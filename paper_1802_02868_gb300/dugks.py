@@ -115,7 +115,7 @@ class Diag_t(ctypes.Structure):
 
 _lib = None
 EXPORTS = ("dugks_create", "dugks_batch_create", "dugks_destroy", "dugks_init", "dugks_step", "dugks_moments",
-           "dugks_conservation", "dugks_batch_status", "dugks_dt", "dugks_info", "dugks_save", "dugks_load",
+           "dugks_conservation", "dugks_conservation_async", "dugks_conservation_wait", "dugks_batch_status", "dugks_dt", "dugks_info", "dugks_save", "dugks_load",
            "dugks_launch_count", "dugks_set_timing", "dugks_kernel_times", "dugks_kernel_name",
            "dugks_kernel_bytes_per_cell", "dugks_status_str", "dugks_conservation_static",
            "dugks_autotune", "dugks_set_tile_shape", "dugks_tile_shape", "dugks_tile_shape_name",
@@ -147,6 +147,8 @@ def load(build_if_missing: bool = True):
     L.dugks_step.argtypes = [vp, ctypes.c_long]
     L.dugks_moments.argtypes = [vp, dp, dp, dp, dp, dp]
     L.dugks_conservation.argtypes = [vp, dp, dp]
+    L.dugks_conservation_async.argtypes = [vp, dp]
+    L.dugks_conservation_wait.argtypes = [vp]
     L.dugks_batch_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int)]
     L.dugks_dt.argtypes = [vp, ip, dp]
     L.dugks_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_long),
@@ -300,6 +302,21 @@ class Sim:
         a, b = np.zeros(n), np.zeros(n)
         _check("dugks_conservation", load().dugks_conservation(self.h, _dp(a), _dp(b)))
         return (a[0], b[0]) if self.single else (a, b)
+
+    def conservation_async(self, sums):
+        """dugks_conservation_async: enqueue the FP64 sums into `sums`, a
+        page-locked float64 array of 2 n_instances values (sum phi, sum rho
+        per instance), and return at once; read it after conservation_wait."""
+        n = len(self.meshes)
+        if sums.dtype != np.float64 or sums.size != 2 * n or not sums.flags.c_contiguous:
+            raise ValueError("sums must be a C-contiguous float64 array of %d values" % (2 * n))
+        _check("dugks_conservation_async", load().dugks_conservation_async(self.h, _dp(sums)))
+        return sums
+
+    def conservation_wait(self):
+        """dugks_conservation_wait: block until the latest conservation_async
+        has landed (the stream keeps running what was enqueued after it)."""
+        _check("dugks_conservation_wait", load().dugks_conservation_wait(self.h))
 
     def status(self):
         n = len(self.meshes)

@@ -79,3 +79,11 @@ def test_set_allocator_needs_both_callbacks():
     dugks.set_allocator(lambda n, st: 0, lambda p, st: None)
     dugks.set_allocator()
     assert dugks._allocator is None
+
+
+def test_async_conservation_rejects_null_arguments():
+    """dugks_conservation_async / _wait check their pointers before any device
+    call (host-only)."""
+    L = dugks.load()
+    assert L.dugks_conservation_async(None, None) == -1
+    assert L.dugks_conservation_wait(None) == -1

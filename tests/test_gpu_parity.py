@@ -269,6 +269,43 @@ def test_every_shape_is_bit_identical_on_uniform_periodic_meshes(prec):
 
 
 @pytest.mark.parametrize("prec", [dugks.FP64, dugks.FP32])
+def test_async_conservation_equals_the_synchronous_sums(prec):
+    """dugks_conservation_async, pipelined as a caller would (enqueue step k + 1,
+    then wait for the sums of step k), returns the bits of dugks_conservation
+    after every step; pageable memory is refused; a wait with nothing pending
+    returns at once."""
+    import torch
+    cases = [CASES[0][1], CASES[3][1], CASES[5][1]]
+    n = len(cases)
+    a = dugks.Sim([c.mesh for c in cases], [c.params for c in cases], prec).init([c.phi0 for c in cases])
+    b = dugks.Sim([c.mesh for c in cases], [c.params for c in cases], prec).init([c.phi0 for c in cases])
+    b.conservation_wait()
+    with pytest.raises(dugks.DugksError) as e:
+        b.conservation_async(np.zeros(2 * n))
+    assert e.value.rc == -1
+    ref = []
+    for _ in range(6):
+        a.step(1)
+        sp, sr = a.conservation()
+        ref.append(np.stack([sp, sr], axis=1).reshape(-1))
+    bufs = [torch.empty(2 * n, dtype=torch.float64).pin_memory().numpy() for _ in range(2)]
+    got = []
+    b.step(1)
+    b.conservation_async(bufs[0])
+    for k in range(1, 6):
+        b.step(1)
+        b.conservation_wait()
+        got.append(bufs[(k - 1) % 2].copy())
+        b.conservation_async(bufs[k % 2])
+    b.conservation_wait()
+    got.append(bufs[1].copy())
+    for r, g in zip(ref, got):
+        assert np.array_equal(r, g)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("prec", [dugks.FP64, dugks.FP32])
 def test_default_shape_follows_the_strip_count(prec):
     """A new sim starts with the 16-block strip when there are at least three
     such strips per resident slot (2 per SM in FP32, 1 in FP64), else with the
