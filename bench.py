@@ -120,12 +120,12 @@ class Clocks:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, tag="bench"):
         self.index = index
         self.p = None
         # raw samples: DUGKS_CLOCKS_DIR if set, else the temporary directory
         folder = os.environ.get("DUGKS_CLOCKS_DIR") or tempfile.gettempdir()
-        self.path = os.path.join(folder, "clocks_bench_%d.csv" % os.getpid())
+        self.path = os.path.join(folder, "clocks_%s_%d.csv" % (tag, os.getpid()))
 
     def start(self):
         try:
@@ -406,10 +406,13 @@ def main():
     out_h = [torch.empty(ncells, dtype=torch.float64).pin_memory() for _ in range(5)]
     sums_h = [torch.empty(2 * len(cases), dtype=torch.float64).pin_memory().numpy() for _ in range(2)]
     drift = 0.0
+    clocks_e2e = Clocks(local, "e2e")
+    clocks_e2e.start()
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    sim.init(phi_h.numpy())
+    sim.init(phi_h.numpy())   # synchronises (device-side finiteness check of phi)
+    t_init = time.perf_counter()
     sim.step(1)
     sim.conservation_async(sums_h[0])
     first = None
@@ -424,9 +427,12 @@ def main():
             drift = max(drift, float(np.nanmax(np.abs(got[0::2] - first) / np.maximum(np.abs(first), 1e-300))))
         if k < args.steps:
             sim.conservation_async(sums_h[k % 2])
+    t_steps = time.perf_counter()   # the last sums have landed: every step is done
     sim.moments(out=[o.numpy() for o in out_h])   # straight into the pinned buffers
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
+    t_end = time.perf_counter()
+    clk_e2e = clocks_e2e.stop()
+    e2e_s = t_end - t0
     e2e_s = max_over_ranks(e2e_s, dist, "cuda")
     n_inst = len(cases)
     h2d = ncells * 8 / args.steps
@@ -434,6 +440,8 @@ def main():
     e2e = {"value": job_rate(args.steps * ncells, ws, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h,
            "phi_sum_drift": drift,
+           "parts_ms": {"init": (t_init - t0) * 1e3, "steps": (t_steps - t_init) * 1e3, "moments": (t_end - t_steps) * 1e3},
+           "clocks": clk_e2e,
            "note": "init from pinned host phi + K steps each followed by a conservation read-back (pipelined: "
                    "step k+1 runs while the host reads the sums of step k) + moments to host"}
 
