@@ -52,7 +52,7 @@ __device__ __forceinline__ double diag_nan() { return __longlong_as_double(0x7ff
 // P if asked).
 constexpr int DIAG_SB = 8;
 template <typename T>
-__global__ void __launch_bounds__(TX *TY) k_diag_f(const InstDev *__restrict__ insts, const int4 *__restrict__ strips,
+__global__ void __launch_bounds__(TX *TY, sizeof(T) == sizeof(float) ? 4 : 2) k_diag_f(const InstDev *__restrict__ insts, const int4 *__restrict__ strips,
                                                    const AxisRecT<T> *__restrict__ geoT, const AxisRec *__restrict__ geo,
                                                    Planes<T> P, DiagPart *parts, double *p_dense,
                                                    const long long *__restrict__ dense0)
@@ -68,9 +68,13 @@ __global__ void __launch_bounds__(TX *TY) k_diag_f(const InstDev *__restrict__ i
     __shared__ T red[TX * TY / 32][DIAG_SUMS];
     __shared__ unsigned long long s_front, s_tip;
     __shared__ int s_ncross;
+    // the instance's parameters and phase constants, read by every cell: one
+    // shared copy instead of a global load per use
+    __shared__ ParT<T> sPr;
+    __shared__ PhiC sC[3];
     const int4 st = strips[blockIdx.x];
     const InstDev &I = insts[st.x];
-    const ParT<T> &Pr = par<T>(I);
+    const ParT<T> &Pr = sPr;   // filled before the first barrier
     const int i0 = st.y, j0 = st.z, nb = st.w;
     const int tid = threadIdx.y * TX + threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool live = !(P.status[st.x] & ST_NONFINITE);
@@ -91,7 +95,12 @@ __global__ void __launch_bounds__(TX *TY) k_diag_f(const InstDev *__restrict__ i
         s_front = 0ull;
         s_tip = 0x7ff0000000000000ull;   // +inf
         s_ncross = 0;
+        sC[0] = I.cA;
+        sC[1] = I.cB;
+        sC[2] = I.cM;
     }
+    static_assert(sizeof(ParT<T>) % sizeof(T) == 0 && sizeof(ParT<T>) / sizeof(T) <= TX * TY, "parameter copy");
+    if (tid < (int)(sizeof(ParT<T>) / sizeof(T))) ((T *)&sPr)[tid] = ((const T *)&par<T>(I))[tid];
     const int x = threadIdx.x, y = threadIdx.y;
     const int i = i0 + x;
     // tilde f of the thread's cell in tile rb
@@ -150,7 +159,7 @@ __global__ void __launch_bounds__(TX *TY) k_diag_f(const InstDev *__restrict__ i
                 const phi_t<T> p0 = sphi[i2(xx, yy)];
                 const T lap = (gx(3, xx) * phi_sub(sphi[i2(xx + smo[xx + 2], yy)], p0) + gx(4, xx) * phi_sub(sphi[i2(xx + spo[xx + 2], yy)], p0))
                             + (gy(3, yy) * phi_sub(sphi[i2(xx, yy + smo[W2 + yy + 2])], p0) + gy(4, yy) * phi_sub(sphi[i2(xx, yy + spo[W2 + yy + 2])], p0));
-                const T dpsi = T(4) * Pr.beta * phi_subc(p0, I.cA) * phi_subc(p0, I.cB) * phi_subc(p0, I.cM);
+                const T dpsi = T(4) * Pr.beta * phi_subc(p0, sC[0]) * phi_subc(p0, sC[1]) * phi_subc(p0, sC[2]);
                 mu = dpsi - Pr.kappa * lap;
             }
             smu[r] = mu;
@@ -180,7 +189,7 @@ __global__ void __launch_bounds__(TX *TY) k_diag_f(const InstDev *__restrict__ i
             const T gfy = gy(0, yr) * fym + gy(1, yr) * fyp;
             const T lmu = (gx(3, x) * smu[i1(xm, yr)] + gx(5, x) * mu + gx(4, x) * smu[i1(xp, yr)])
                         + (gy(3, yr) * smu[i1(x, ym)] + gy(5, yr) * mu + gy(4, yr) * smu[i1(x, yp)]);
-            const T rho = rho_of<T>(I, phi);
+            const T rho = Pr.rhoB + Pr.drho * (phi - Pr.phiB);   // Eq. (oderrho), as rho_of forms it
             const T Fx = -phi * gmx + (rho - Pr.rho_ref) * Pr.gxa;
             const T Fy = -phi * gmy + (rho - Pr.rho_ref) * Pr.gya;
             T sf = 0, mx = 0, my = 0;
