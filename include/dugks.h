@@ -223,6 +223,11 @@ int dugks_kernel_bytes_per_cell(const dugks_sim *sim, int k, double *bytes);
 #define DUGKS_NUM_TILE_SHAPES 7
 int dugks_autotune(dugks_sim *sim, int steps, int *chosen, double *ms_per_step);
 int dugks_set_tile_shape(dugks_sim *sim, int shape);
+/* The shape a new fused-step sim of these meshes starts with (the rule above),
+   without a device: nx, ny are host arrays of n_instances mesh sizes, n_sm the
+   device's multiprocessor count (152 on GB300).  DUGKS_ERR_ARG for a null
+   pointer, a size or count below 1, or an unknown precision. */
+int dugks_default_tile_shape(const int *nx, const int *ny, int n_instances, int precision, int n_sm, int *shape);
 int dugks_tile_shape(const dugks_sim *sim, int *shape, int *bx, int *by);
 const char *dugks_tile_shape_name(int shape);
 

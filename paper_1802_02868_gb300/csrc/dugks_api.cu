@@ -324,18 +324,28 @@ int prepare_strip()
 // 16-instance batch (608 strips for 304 slots), and the 16-block strip from
 // 2048x2048 (1024 strips) and the 64-instance batch on; the thresholds below
 // reproduce those choices, and dugks_autotune measures the rest.
-int default_shape(const dugks_sim *s)
+int shape_for_sizes(const int *nx, const int *ny, int n, int precision, int n_sm)
 {
-    if (!s->fused) return 0;
-    const long long slots = (long long)s->n_sm * (s->prec == DUGKS_FP64 ? 1 : 2);
+    const long long slots = (long long)n_sm * (precision == DUGKS_FP64 ? 1 : 2);
     auto strips = [&](int nb) {
         long long c = 0;
-        for (const InstDev &I : s->h_inst) c += (long long)((I.nx + 31) / 32) * ((I.ny + 8 * nb - 1) / (8 * nb));
+        for (int k = 0; k < n; k++) c += (long long)((nx[k] + 31) / 32) * ((ny[k] + 8 * nb - 1) / (8 * nb));
         return c;
     };
     if (strips(kShapes[5].nb) >= 3 * slots) return 5;
     if (strips(kShapes[4].nb) >= 2 * slots) return 4;
     return 0;
+}
+
+int default_shape(const dugks_sim *s)
+{
+    if (!s->fused) return 0;
+    std::vector<int> nx, ny;
+    for (const InstDev &I : s->h_inst) {
+        nx.push_back(I.nx);
+        ny.push_back(I.ny);
+    }
+    return shape_for_sizes(nx.data(), ny.data(), s->n_inst, s->prec, s->n_sm);
 }
 
 // fused-step tile table of shape k: the uniform periodic instances' tiles first
@@ -1585,6 +1595,16 @@ int dugks_uniform_instances(const dugks_sim *s, int *n)
     int k = 0;
     for (const InstDev &I : s->h_inst) k += (s->use_uni && I.uni) ? 1 : 0;
     *n = k;
+    return DUGKS_OK;
+}
+
+int dugks_default_tile_shape(const int *nx, const int *ny, int n_instances, int precision, int n_sm, int *shape)
+{
+    if (!nx || !ny || !shape || n_instances < 1 || n_sm < 1) return DUGKS_ERR_ARG;
+    if (precision != DUGKS_FP64 && precision != DUGKS_FP32) return DUGKS_ERR_ARG;
+    for (int k = 0; k < n_instances; k++)
+        if (nx[k] < 1 || ny[k] < 1) return DUGKS_ERR_ARG;
+    *shape = shape_for_sizes(nx, ny, n_instances, precision, n_sm);
     return DUGKS_OK;
 }
 

@@ -118,7 +118,7 @@ EXPORTS = ("dugks_create", "dugks_batch_create", "dugks_destroy", "dugks_init", 
            "dugks_conservation", "dugks_conservation_async", "dugks_conservation_wait", "dugks_batch_status", "dugks_dt", "dugks_info", "dugks_save", "dugks_load",
            "dugks_launch_count", "dugks_set_timing", "dugks_kernel_times", "dugks_kernel_name",
            "dugks_kernel_bytes_per_cell", "dugks_status_str", "dugks_conservation_static",
-           "dugks_autotune", "dugks_set_tile_shape", "dugks_tile_shape", "dugks_tile_shape_name",
+           "dugks_autotune", "dugks_set_tile_shape", "dugks_tile_shape", "dugks_tile_shape_name", "dugks_default_tile_shape",
            "dugks_adjoint", "dugks_uniform_instances", "dugks_diagnostics", "dugks_laplace_pressure",
            "dugks_batch_set_paused", "dugks_batch_step_each", "dugks_set_allocator", "dugks_measure_alu_peaks")
 STATIC_MAX_CELLS = 16777216
@@ -174,6 +174,7 @@ def load(build_if_missing: bool = True):
     L.dugks_set_allocator.argtypes = [ALLOC_FN, FREE_FN, vp]
     L.dugks_measure_alu_peaks.argtypes = [ip, ip, dp, dp, dp, vp]
     L.dugks_tile_shape_name.argtypes = [ip]
+    L.dugks_default_tile_shape.argtypes = [ctypes.POINTER(ctypes.c_int)] * 2 + [ip, ip, ip, ctypes.POINTER(ctypes.c_int)]
     L.dugks_tile_shape_name.restype = ctypes.c_char_p
     L.dugks_status_str.argtypes = [ip]
     L.dugks_status_str.restype = ctypes.c_char_p
@@ -464,6 +465,18 @@ def measure_alu_peaks(iters_f32=262144, iters_f64=4096, stream=0):
 
 
 NUM_TILE_SHAPES = 7
+
+
+def default_tile_shape(meshes, precision=FP32, n_sm=152):
+    """dugks_default_tile_shape: the shape a new fused-step sim of these meshes
+    starts with on a device of n_sm multiprocessors (no device needed)."""
+    meshes = list(meshes) if isinstance(meshes, (list, tuple)) else [meshes]
+    nx = (ctypes.c_int * len(meshes))(*[m.nx for m in meshes])
+    ny = (ctypes.c_int * len(meshes))(*[m.ny for m in meshes])
+    k = ctypes.c_int()
+    _check("dugks_default_tile_shape",
+           load().dugks_default_tile_shape(nx, ny, len(meshes), int(precision), int(n_sm), ctypes.byref(k)))
+    return k.value
 
 
 def tile_shape_name(k):

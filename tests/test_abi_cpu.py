@@ -87,3 +87,46 @@ def test_async_conservation_rejects_null_arguments():
     L = dugks.load()
     assert L.dugks_conservation_async(None, None) == -1
     assert L.dugks_conservation_wait(None) == -1
+
+
+def test_default_tile_shape_rule_on_the_host():
+    """dugks_default_tile_shape, the rule dugks_batch_create applies: the
+    16-block strip at >= 3 strips of 16 blocks (32 x 128 cells) per resident
+    slot, else the 8-block strip at >= 2 strips of 8 blocks (32 x 64 cells)
+    per slot, else the 32x8 tile.  A GB300 has 152 SMs: 304 FP32 slots (two
+    strip blocks per SM), 152 FP64 slots.  Strip counts worked out by hand."""
+    m = I.uniform_mesh
+    f32, f64 = dugks.FP32, dugks.FP64
+    assert dugks.default_tile_shape([m(256, 1024)], f32) == 0      # 8 x 8 = 64 of 16; 8 x 16 = 128 of 8
+    assert dugks.default_tile_shape([m(1024, 1024)], f32) == 0     # 32 x 8 = 256 < 912; 32 x 16 = 512 < 608
+    assert dugks.default_tile_shape([m(1536, 1536)], f32) == 4     # 48 x 12 = 576 < 912; 48 x 24 = 1152
+    assert dugks.default_tile_shape([m(2048, 2048)], f32) == 5     # 64 x 16 = 1024 >= 912
+    assert dugks.default_tile_shape([m(1024, 1024)], f64) == 4     # 256 < 456; 512 >= 304
+    assert dugks.default_tile_shape([m(2048, 2048)], f64) == 5
+    assert dugks.default_tile_shape([m(512, 512)], f64) == 0       # 16 x 8 = 128 of 8 < 304
+    # the thresholds themselves: a 32 x 128 mesh is one strip of 16 and two of 8
+    assert dugks.default_tile_shape([m(32, 128)] * 912, f32) == 5
+    assert dugks.default_tile_shape([m(32, 128)] * 911, f32) == 4
+    assert dugks.default_tile_shape([m(32, 128)] * 304, f32) == 4
+    assert dugks.default_tile_shape([m(32, 128)] * 303, f32) == 0
+    # ragged sizes round up: 33 x 129 is 2 x 2 strips of 16 and 2 x 3 of 8
+    assert dugks.default_tile_shape([m(33, 129)] * 228, f32) == 5  # 912 strips of 16
+    assert dugks.default_tile_shape([m(33, 129)] * 102, f32) == 4  # 408 of 16, 612 of 8
+    assert dugks.default_tile_shape([m(33, 129)] * 101, f32) == 0  # 606 of 8
+    # another device size scales the slots
+    assert dugks.default_tile_shape([m(1024, 1024)], f32, n_sm=64) == 4   # 512 >= 256 of 8, 256 < 384 of 16
+    assert dugks.default_tile_shape([m(1024, 1024)], f32, n_sm=32) == 5   # 256 >= 192
+
+
+def test_default_tile_shape_rejects_bad_arguments():
+    L = dugks.load()
+    nx = (ctypes.c_int * 1)(64)
+    ny = (ctypes.c_int * 1)(64)
+    k = ctypes.c_int()
+    assert L.dugks_default_tile_shape(nx, ny, 1, dugks.FP32, 0, ctypes.byref(k)) == -1
+    assert L.dugks_default_tile_shape(nx, ny, 0, dugks.FP32, 152, ctypes.byref(k)) == -1
+    assert L.dugks_default_tile_shape(nx, ny, 1, 7, 152, ctypes.byref(k)) == -1
+    assert L.dugks_default_tile_shape(None, ny, 1, dugks.FP32, 152, ctypes.byref(k)) == -1
+    zero = (ctypes.c_int * 1)(0)
+    assert L.dugks_default_tile_shape(zero, ny, 1, dugks.FP32, 152, ctypes.byref(k)) == -1
+    assert L.dugks_default_tile_shape(nx, ny, 1, dugks.FP32, 152, ctypes.byref(k)) == 0 and k.value == 0

@@ -323,6 +323,7 @@ def test_default_shape_follows_the_strip_count(prec):
         want = 5 if strips(cases, 16) >= 3 * slots else 4 if strips(cases, 8) >= 2 * slots else 0
         s = dugks.Sim([c.mesh for c in cases], [c.params for c in cases], prec)
         assert s.tile_shape()[0] == want, (len(cases), want)
+        assert dugks.default_tile_shape([c.mesh for c in cases], prec, n_sm) == want
         s.close()
         seen.add(want)
     assert 0 in seen and len(seen) >= 2
