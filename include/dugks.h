@@ -241,7 +241,9 @@ const char *dugks_tile_shape_name(int shape);
 int dugks_uniform_instances(const dugks_sim *sim, int *n);
 
 /* Diagnostics of the current state of every instance, computed on the device
-   in FP64 (the paper's test quantities; c = (phi - phiB)/(phiA - phiB)):
+   (the paper's test quantities; c = (phi - phiB)/(phiA - phiB)).  FP64 sims
+   work in FP64; FP32 sims form the cell quantities and each 32 x 64 strip's
+   sums in FP32 and add the strips in FP64; the results are FP64:
      mass        total volume of the cells with c > 1/2: the droplet mass of
                  Sec. 3.1, Table A1 (a cell count on a unit mesh)
      xc, yc      centroid of that region (coordinates with the low faces at

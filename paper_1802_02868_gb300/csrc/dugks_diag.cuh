@@ -1,4 +1,4 @@
-// dugks_diag.cuh -- on-device diagnostics of a state, in FP64.
+// dugks_diag.cuh -- on-device diagnostics of a state.
 //
 //   Laplace pressure (Sec. 3.1, Laplace's law):
 //       P = p0 - kappa phi lap(phi) + kappa |grad phi|^2 / 2 + p,
@@ -14,8 +14,8 @@
 //   placed by linear interpolation between the centres; the highest and the
 //   lowest crossing (pairs across a periodic y boundary do not count).
 //
-// k_diag_f forms per-tile partial sums and extremes in one pass over the
-// state; k_diag_inst adds the tiles of each instance in tile order, so the
+// k_diag_f forms per-strip partial sums and extremes in one pass over the
+// state; k_diag_inst adds the strips of each instance in strip order, so the
 // result does not depend on timing.
 #pragma once
 #include "dugks_fused.cuh"
@@ -35,8 +35,8 @@ struct DiagOut {
 
 __device__ __forceinline__ double diag_nan() { return __longlong_as_double(0x7ff8000000000000LL); }
 
-// Arithmetic in the sim's precision T: FP32 sims sum each tile in FP32 (the
-// FP64 pipe of GB300 runs at 1/64 of the FP32 rate) and the tiles of an
+// Arithmetic in the sim's precision T: FP32 sims sum each strip in FP32 (the
+// FP64 pipe of GB300 runs at 1/64 of the FP32 rate) and the strips of an
 // instance in FP64; the crossing heights are placed and compared in FP64.
 // The sums of each tile of a strip of up to SB tiles (32 columns, 8 SB rows)
 // in one pass over the state.  A block stages phi of the strip and a
