@@ -268,9 +268,9 @@ int dugks_diagnostics(dugks_sim *sim, dugks_diag *out);
 
 /* The Laplace pressure field of Sec. 3.1, P = p0 - kappa phi lap(phi)
    + kappa |grad phi|^2 / 2 + p with p0 = phi psi' - psi and
-   psi = beta (phi - phiA)^2 (phi - phiB)^2, in FP64 on the device; the
-   gradients use the stencils of Eqs. (nonphi), (nonphi2) with mirror ghosts
-   at walls.  P (host) holds all instances' cells, row-major, in instance
+   psi = beta (phi - phiA)^2 (phi - phiB)^2, on the device in the sim's
+   precision (returned as FP64); the gradients use the stencils of Eqs.
+   (nonphi), (nonphi2) with mirror ghosts at walls.  P (host) holds all instances' cells, row-major, in instance
    order.  Synchronises. */
 int dugks_laplace_pressure(dugks_sim *sim, double *P);
 
