@@ -130,7 +130,9 @@ int dugks_conservation(dugks_sim *sim, double *sum_phi, double *sum_rho);
    DUGKS_ERR_ARG, since its copy could not be asynchronous) and must not be
    read or freed before dugks_conservation_wait returns.  Steps enqueued
    after the call run behind it on the stream, so a caller can enqueue step
-   k + 1 and then wait for the sums of step k while the GPU works. */
+   k + 1 and then wait for the sums of step k while the GPU works.  The first
+   call creates an event and a small page-locked status buffer, which
+   dugks_destroy frees. */
 int dugks_conservation_async(dugks_sim *sim, double *sums);
 
 /* Wait (on an event, not the whole stream) until the sums of the latest
