@@ -8,7 +8,8 @@ kernels not spilling registers:
 - the FP32 32x8 tile (256 threads) for 3 blocks per SM;
 - the FP64 strip and tile for 1.
 A GB300 SM has 228 KB of shared memory, up to 227 KB per block, and reserves
-1 KB per resident block.  The FP32 strip must also compile without spilling.
+1 KB per resident block.  The FP32 strip must also compile without spilling,
+and the FP32 diagnostics kernel within 64 registers.
 """
 import os
 import re
@@ -56,7 +57,10 @@ def test_shared_memory_of_each_shape_fits_its_blocks_per_sm(tmp_path):
     assert _fits(strip64, 1) and _fits(tile64, 1), (strip64, tile64)
 
 
-def test_fp32_strips_compile_without_spills(tmp_path):
+def test_fp32_strips_and_diagnostics_compile_within_budget(tmp_path):
+    """The FP32 strips spill nothing; the FP32 diagnostics kernel fits 64
+    registers without spills, which holds four of its 256-thread blocks per
+    SM (its speed rests on that occupancy)."""
     out = tmp_path / "api.o"
     r = subprocess.run([_nvcc(), "-c", os.path.join(CSRC, "dugks_api.cu"), "-o", str(out), "-O3", "-Xptxas", "-v",
                         "-Xcompiler", "-fPIC"] + ARCH + FLAGS, capture_output=True, text=True)
@@ -73,3 +77,10 @@ def test_fp32_strips_compile_without_spills(tmp_path):
                 spill = re.search(r"(\d+) bytes spill stores", props)
                 assert spill is not None and int(spill.group(1)) == 0, (m.group(1), props)
     assert found == {"k_strip": 2}, "expected the general and the uniform FP32 strip: %s" % found
+    diag = [i for i, line in enumerate(lines) if re.search(r"Compiling entry function '\S*k_diag_fIfE", line)]
+    assert len(diag) == 1, diag
+    props = " ".join(lines[diag[0] + 1:diag[0] + 4])
+    spill = re.search(r"(\d+) bytes spill stores", props)
+    regs = re.search(r"Used (\d+) registers", props)
+    assert spill is not None and int(spill.group(1)) == 0, props
+    assert regs is not None and int(regs.group(1)) <= 64, props
